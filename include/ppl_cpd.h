@@ -1,0 +1,162 @@
+/*
+ * ppl_cpd.h -- matrix-free CP-ALS of the DF particle-particle-ladder (PPL) tensor
+ * on one NVIDIA GB300 (sm_103a).  C ABI of libpplcpd.so.
+ *
+ * The method (Pierce, "Towards Using Matrix-Free Tensor Decompositions to
+ * Systematically Improve Approximate Tensor-Networks"):
+ *
+ *   R[a,b,i,j] = sum_{Q,c,d} B[Q,a,c] B[Q,b,d] tau[i,j,c,d]          Eq. (dfB), D-bar = D
+ *   R~[a,b,i,j] = sum_r lam[r] Ua[a,r] Ub[b,r] Ui[i,r] Uj[j,r]        Eq. (cp-ppl)
+ *
+ * R is never formed.  Each ALS sweep updates Ua, Ub, Ui, Uj in that order
+ * (Optimizing the CP-PPL tensor-network section): a matrix-free MTTKRP
+ * (Eqs. full_der, distribute, foreachr), the Hadamard product V of the other
+ * three Gram matrices, a Cholesky solve U~ = M V^-1, and a column
+ * normalisation into lam.  The fit follows Eq. (cpfit) with the residual
+ * expansion and Eq. (cp_norm2).
+ *
+ * Conventions for every call below:
+ *  - Tensor arguments are DEVICE pointers, allocated and owned by the caller;
+ *    the library never frees them and keeps using B and tau until
+ *    ppl_cpd_destroy (or ppl_cpd_set_tau for tau).  All arrays are dense,
+ *    row-major, FP64.
+ *  - `stream` is a cudaStream_t passed as void*; all device work of a handle
+ *    is issued on it.  Calls that return host scalars synchronise that stream.
+ *  - Every call returns a PPL_* status; on error, ppl_last_error(h) (or
+ *    ppl_last_error(NULL) before a handle exists) gives a message.  No call
+ *    aborts the process.  A non-positive-definite V is not an error: its
+ *    clamped pivots are counted (ppl_cpd_stats).
+ *  - The library allocates no device memory: everything it needs lives in
+ *    the caller's workspace (ppl_cpd_workspace_size, then ppl_cpd_init).
+ */
+#ifndef PPL_CPD_H
+#define PPL_CPD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPL_OK        0
+#define PPL_EINVAL    1   /* bad argument (NULL pointer, size out of range)          */
+#define PPL_ENOMEM    2   /* workspace smaller than ppl_cpd_workspace_size          */
+#define PPL_ECUDA     3   /* a CUDA runtime call failed                             */
+#define PPL_ETIMEOUT  4   /* a bounded device wait expired; the kernel returned     */
+#define PPL_ENOTREADY 5   /* fit asked for before ||R||^2 or before any sweep       */
+
+/* arithmetic of the MTTKRP contractions; Gram, solve, fit and energy are FP64 always */
+#define PPL_PREC_FP64   0  /* plain FP64 on the CUDA cores                                 */
+#define PPL_PREC_BF16X3 1  /* tcgen05 BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accum. */
+#define PPL_PREC_TF32   2  /* tcgen05 TF32 (round-to-nearest operands), FP32 accumulate    */
+
+#define PPL_MODE_A 0  /* alpha, first virtual index  */
+#define PPL_MODE_B 1  /* beta, second virtual index  */
+#define PPL_MODE_I 2  /* gamma, first occupied index  */
+#define PPL_MODE_J 3  /* rho, second occupied index   */
+
+typedef struct ppl_cpd ppl_cpd;   /* opaque handle, host memory owned by the library */
+
+typedef struct {
+    int precision;   /* PPL_PREC_*                                                       */
+    int r_chunk;     /* columns of r processed per pass of the fused chain; 0 = automatic */
+    int use_graph;   /* 1: capture one sweep in a CUDA graph on first use and replay it  */
+    int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
+    int reserved[12];
+} ppl_cpd_opts;
+
+typedef struct {
+    long long sweeps;          /* sweeps run since init                                   */
+    long long clamped_pivots;  /* Cholesky pivots replaced by the tolerance, all solves   */
+    long long timeouts;        /* bounded device waits that expired                       */
+    double    last_fit;        /* fit after the last sweep (NaN if ||R||^2 unknown)       */
+    double    last_eta;        /* eta after the last sweep (NaN unless want_eta)          */
+    double    last_inner;      /* <R, R~> after the last sweep                            */
+    double    last_norm2;      /* ||R~||^2 after the last sweep, Eq. (cp_norm2)           */
+    double    flops_per_sweep; /* algorithmic MTTKRP flops per sweep, 4 o^2 v^2 R + 16 X v^2 R */
+} ppl_cpd_stats;
+
+/* Fill *opts with defaults: BF16X3, automatic r_chunk, graphs on, eta off. */
+void ppl_cpd_default_opts(ppl_cpd_opts* opts);
+
+/* Bytes of device workspace a handle with these sizes and options needs.
+ * o, v, X, R >= 1.  Pure host arithmetic (no CUDA call).  EINVAL on bad sizes. */
+int ppl_cpd_workspace_size(int o, int v, int X, int R, const ppl_cpd_opts* opts, size_t* bytes);
+
+/* Create a handle.
+ *   B        [X][o+v][o+v]  DF factor D^{pX}_q (Eq. SQG), occupied orbitals first,
+ *                           symmetric in p, q (only the symmetric problem is defined).
+ *   tau      [o][o][v][v]   tau[i,j,c,d] = t2 + t1 t1 (Eq. B); pair symmetry is not required.
+ *   factors  Ua[v*R] | Ub[v*R] | Ui[o*R] | Uj[o*R] | lam[R], each [dim][R] row-major.
+ *            In: the initial guess (lam is ignored and set to 1).  The handle
+ *            updates this buffer in place; after a call returns it holds the
+ *            current model with unit-norm columns and the scales in lam.
+ *   workspace, ws_bytes: device memory of at least ppl_cpd_workspace_size bytes,
+ *            256-byte aligned; owned by the caller, used until ppl_cpd_destroy.
+ *   opts     NULL for defaults.
+ * The BF16X3/TF32 operand copies of tau and B are made here (device work on
+ * `stream`). */
+int ppl_cpd_init(ppl_cpd** h, int o, int v, int X, int R,
+                 const double* B, const double* tau, double* factors,
+                 void* workspace, size_t ws_bytes, const ppl_cpd_opts* opts, void* stream);
+
+/* MTTKRP of the current factors for one mode, M_out [dim][R] FP64 device
+ * (dim = v for modes a, b and o for i, j).  Eq. (full_der) numerator:
+ *   M_a[a,r] = sum_{b,i,j} R[a,b,i,j] Ub[b,r] Ui[i,r] Uj[j,r], and likewise.
+ * The factors are not changed. */
+int ppl_cpd_mttkrp(ppl_cpd* h, int mode, double* M_out);
+
+/* Run nsweeps ALS sweeps (a, b, i, j).  fit_hist (HOST, may be NULL) receives
+ * the fit after each sweep, or NaN where ||R||^2 is not known. */
+int ppl_cpd_sweep(ppl_cpd* h, int nsweeps, double* fit_hist);
+
+/* Supply ||R||^2 for the fit (Eq. cpfit) without ppl_exact_contract. */
+int ppl_cpd_set_normR2(ppl_cpd* h, double normR2);
+
+/* Fit after the last sweep: 1 - sqrt(max(0, ||R||^2 - 2<R,R~> + ||R~||^2)) / ||R||.
+ * ENOTREADY if ||R||^2 is unknown or no sweep has run. */
+int ppl_cpd_fit(ppl_cpd* h, double* fit);
+
+/* CP estimate of the PPL energy, E = sum R~[a,b,i,j] (2 g[iajb] - g[ibja]) with
+ * g[iajb] = sum_Q B[Q,i,a] B[Q,j,b], computed without forming R~:
+ *   E = sum_r lam_r sum_Q [2 A_Q(Ui,Ua) A_Q(Uj,Ub) - A_Q(Ui,Ub) A_Q(Uj,Ua)],
+ *   A_Q(x,y)_r = sum_{i,a} B[Q,i,a] x[i,r] y[a,r].                    (FP64) */
+int ppl_cpd_energy(ppl_cpd* h, double* E_cp);
+
+/* Exact contraction of Eq. (dfB), blocked over a: returns ||R||^2 and
+ * E_exact = sum R[a,b,i,j] (2 g[iajb] - g[ibja]) (host scalars, either may be
+ * NULL) and, if R_out != NULL, R itself as [v][v][o][o] (device).  Stores
+ * ||R||^2 in the handle for ppl_cpd_fit.  Cost 2 X v^4 + 2 o^2 v^4 flops, FP64. */
+int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_out);
+
+/* Point the handle at a new tau (same shape, device) for the next CC-like
+ * step; the factors in the caller's buffer are kept as the warm start
+ * (the paper's "Optimal guess", Role of the Initial Guess section).  The
+ * stored ||R||^2 is forgotten. */
+int ppl_cpd_set_tau(ppl_cpd* h, const double* tau);
+
+/* Counters and the last sweep's scalars. */
+int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* stats);
+
+/* Message for the last failed call on h (h may be NULL: errors of init / size
+ * queries).  The string belongs to the library. */
+const char* ppl_last_error(const ppl_cpd* h);
+
+/* Release the handle (host memory and any captured graph).  The caller then
+ * frees its workspace, B, tau and factors.  h may be NULL. */
+int ppl_cpd_destroy(ppl_cpd* h);
+
+/* Building-block check of the tensor-core contraction used by the MTTKRP:
+ * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the
+ * given PPL_PREC_BF16X3 or PPL_PREC_TF32 tcgen05 kernel (operands split or
+ * rounded on the device, FP32 accumulate) and written to C (FP32 device,
+ * [M][N]).  workspace must hold ppl_tc_gemm_workspace_size bytes. */
+int ppl_tc_gemm_workspace_size(int M, int N, int K, int precision, size_t* bytes);
+int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float* B, float* C,
+                void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPL_CPD_H */

@@ -1,0 +1,267 @@
+"""ctypes binding of libpplcpd.so (include/ppl_cpd.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the CP-ALS path runs in
+the library's CUDA kernels.  PyTorch provides device memory and the stream.
+If the library is missing this module raises: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_size_t, c_void_p
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpplcpd.so")
+
+PPL_OK, PPL_EINVAL, PPL_ENOMEM, PPL_ECUDA, PPL_ETIMEOUT, PPL_ENOTREADY = range(6)
+PREC = {"fp64": 0, "bf16x3": 1, "tf32": 2}
+MODE = {"a": 0, "b": 1, "i": 2, "j": 3}
+STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4: "PPL_ETIMEOUT",
+                5: "PPL_ENOTREADY"}
+
+
+class ppl_cpd_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
+                ("reserved", c_int * 12)]
+
+
+class ppl_cpd_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_longlong), ("clamped_pivots", ctypes.c_longlong),
+                ("timeouts", ctypes.c_longlong), ("last_fit", c_double), ("last_eta", c_double),
+                ("last_inner", c_double), ("last_norm2", c_double), ("flops_per_sweep", c_double)]
+
+
+class PplError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpplcpd.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c \"import __graft_entry__ as g; g.build()\"`")
+    L = ctypes.CDLL(LIB_PATH)
+    H = c_void_p
+    L.ppl_cpd_default_opts.argtypes = [POINTER(ppl_cpd_opts)]
+    L.ppl_cpd_default_opts.restype = None
+    L.ppl_cpd_workspace_size.argtypes = [c_int, c_int, c_int, c_int, POINTER(ppl_cpd_opts), POINTER(c_size_t)]
+    L.ppl_cpd_init.argtypes = [POINTER(H), c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_size_t, POINTER(ppl_cpd_opts), c_void_p]
+    L.ppl_cpd_mttkrp.argtypes = [H, c_int, c_void_p]
+    L.ppl_cpd_sweep.argtypes = [H, c_int, POINTER(c_double)]
+    L.ppl_cpd_set_normR2.argtypes = [H, c_double]
+    L.ppl_cpd_fit.argtypes = [H, POINTER(c_double)]
+    L.ppl_cpd_energy.argtypes = [H, POINTER(c_double)]
+    L.ppl_exact_contract.argtypes = [H, POINTER(c_double), POINTER(c_double), c_void_p]
+    L.ppl_cpd_set_tau.argtypes = [H, c_void_p]
+    L.ppl_cpd_stats_get.argtypes = [H, POINTER(ppl_cpd_stats)]
+    L.ppl_last_error.argtypes = [H]
+    L.ppl_last_error.restype = c_char_p
+    L.ppl_cpd_destroy.argtypes = [H]
+    L.ppl_tc_gemm_workspace_size.argtypes = [c_int, c_int, c_int, c_int, POINTER(c_size_t)]
+    L.ppl_tc_gemm.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                              c_void_p]
+    for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
+                 "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
+                 "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy",
+                 "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
+        getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, h=None):
+    if rc != PPL_OK:
+        msg = lib().ppl_last_error(h)
+        raise PplError(rc, msg.decode() if msg else "")
+
+
+def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False) -> ppl_cpd_opts:
+    o = ppl_cpd_opts()
+    lib().ppl_cpd_default_opts(ctypes.byref(o))
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.r_chunk = int(r_chunk)
+    o.use_graph = int(bool(use_graph))
+    o.want_eta = int(bool(want_eta))
+    return o
+
+
+# ---- thin wrappers, one per C entry point ------------------------------------
+
+def ppl_cpd_workspace_size(o, v, X, R, opts: ppl_cpd_opts) -> int:
+    n = c_size_t(0)
+    _check(lib().ppl_cpd_workspace_size(o, v, X, R, ctypes.byref(opts), ctypes.byref(n)))
+    return n.value
+
+
+def ppl_cpd_init(o, v, X, R, B_ptr, tau_ptr, factors_ptr, ws_ptr, ws_bytes, opts, stream_ptr) -> c_void_p:
+    h = c_void_p()
+    _check(lib().ppl_cpd_init(ctypes.byref(h), o, v, X, R, B_ptr, tau_ptr, factors_ptr, ws_ptr, ws_bytes,
+                              ctypes.byref(opts), stream_ptr))
+    return h
+
+
+def ppl_cpd_mttkrp(h, mode: int, M_ptr):
+    _check(lib().ppl_cpd_mttkrp(h, mode, M_ptr), h)
+
+
+def ppl_cpd_sweep(h, nsweeps: int, want_hist: bool = True):
+    buf = (c_double * max(nsweeps, 1))() if want_hist else None
+    _check(lib().ppl_cpd_sweep(h, nsweeps, buf), h)
+    return list(buf)[:nsweeps] if want_hist else None
+
+
+def ppl_cpd_set_normR2(h, normR2: float):
+    _check(lib().ppl_cpd_set_normR2(h, float(normR2)), h)
+
+
+def ppl_cpd_fit(h) -> float:
+    x = c_double()
+    _check(lib().ppl_cpd_fit(h, ctypes.byref(x)), h)
+    return x.value
+
+
+def ppl_cpd_energy(h) -> float:
+    x = c_double()
+    _check(lib().ppl_cpd_energy(h, ctypes.byref(x)), h)
+    return x.value
+
+
+def ppl_exact_contract(h, R_ptr=None):
+    n2, E = c_double(), c_double()
+    _check(lib().ppl_exact_contract(h, ctypes.byref(n2), ctypes.byref(E), R_ptr), h)
+    return n2.value, E.value
+
+
+def ppl_cpd_set_tau(h, tau_ptr):
+    _check(lib().ppl_cpd_set_tau(h, tau_ptr), h)
+
+
+def ppl_cpd_stats_get(h) -> dict:
+    s = ppl_cpd_stats()
+    _check(lib().ppl_cpd_stats_get(h, ctypes.byref(s)), h)
+    return {k: getattr(s, k) for k, _ in ppl_cpd_stats._fields_}
+
+
+def ppl_cpd_destroy(h):
+    _check(lib().ppl_cpd_destroy(h))
+
+
+def ppl_tc_gemm_workspace_size(M, N, K, precision) -> int:
+    n = c_size_t(0)
+    _check(lib().ppl_tc_gemm_workspace_size(M, N, K, precision, ctypes.byref(n)))
+    return n.value
+
+
+def ppl_tc_gemm(precision, M, N, K, A_ptr, B_ptr, C_ptr, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().ppl_tc_gemm(precision, M, N, K, A_ptr, B_ptr, C_ptr, ws_ptr, ws_bytes, stream_ptr))
+
+
+# ---- torch-facing convenience object ------------------------------------------
+
+class CpAls:
+    """One CP-ALS problem on the current CUDA device.
+
+    B [X][o+v][o+v] and tau [o][o][v][v] are FP64 device tensors (kept alive
+    here); `factors` is a dict of initial guesses "a","b" [v][R] and "i","j"
+    [o][R] (numpy or torch).  torch allocates the factor buffer and the
+    workspace; the library does the rest.
+    """
+
+    def __init__(self, B, tau, factors, precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False,
+                 stream=None):
+        import torch
+        self.torch = torch
+        X, n, _ = B.shape
+        o = tau.shape[0]
+        v = tau.shape[2]
+        R = factors["a"].shape[1]
+        assert n == o + v and B.dtype == torch.float64 and tau.dtype == torch.float64 and B.is_cuda
+        self.o, self.v, self.X, self.R = o, v, X, R
+        self.B = B.contiguous()
+        self.tau = tau.contiguous()
+        dev = B.device
+        parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
+        parts.append(torch.ones(R, dtype=torch.float64))
+        self.fac = torch.cat(parts).to(dev)
+        self.opts = make_opts(precision, r_chunk, use_graph, want_eta)
+        self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.h = ppl_cpd_init(o, v, X, R, self.B.data_ptr(), self.tau.data_ptr(), self.fac.data_ptr(),
+                              self.ws.data_ptr(), self.ws_bytes, self.opts, self.stream.cuda_stream)
+
+    def factors(self) -> dict:
+        o, v, R = self.o, self.v, self.R
+        f = self.fac
+        out, pos = {}, 0
+        for m, dim in (("a", v), ("b", v), ("i", o), ("j", o)):
+            out[m] = f[pos:pos + dim * R].view(dim, R)
+            pos += dim * R
+        out["lam"] = f[pos:pos + R]
+        return out
+
+    def mttkrp(self, mode: str):
+        dim = self.v if mode in "ab" else self.o
+        M = self.torch.empty((dim, self.R), dtype=self.torch.float64, device=self.B.device)
+        ppl_cpd_mttkrp(self.h, MODE[mode], M.data_ptr())
+        return M
+
+    def sweep(self, n: int = 1, want_hist: bool = True):
+        return ppl_cpd_sweep(self.h, n, want_hist)
+
+    def set_normR2(self, x: float):
+        ppl_cpd_set_normR2(self.h, x)
+
+    def fit(self) -> float:
+        return ppl_cpd_fit(self.h)
+
+    def energy(self) -> float:
+        return ppl_cpd_energy(self.h)
+
+    def exact_contract(self, want_R: bool = False):
+        Rt = None
+        if want_R:
+            Rt = self.torch.empty((self.v, self.v, self.o, self.o), dtype=self.torch.float64, device=self.B.device)
+        n2, E = ppl_exact_contract(self.h, Rt.data_ptr() if Rt is not None else None)
+        return n2, E, Rt
+
+    def set_tau(self, tau):
+        self.tau = tau.contiguous()
+        ppl_cpd_set_tau(self.h, self.tau.data_ptr())
+
+    def stats(self) -> dict:
+        return ppl_cpd_stats_get(self.h)
+
+    def close(self):
+        if self.h:
+            ppl_cpd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tc_gemm(A, B, precision="bf16x3"):
+    """C = A @ B^T for FP32 CUDA tensors through the tensor-core kernel."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    prec = PREC[precision]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    nbytes = ppl_tc_gemm_workspace_size(M, N, K, prec)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
+    ppl_tc_gemm(prec, M, N, K, A.contiguous().data_ptr(), B.contiguous().data_ptr(), C.data_ptr(),
+                ws.data_ptr(), nbytes, torch.cuda.current_stream(A.device).cuda_stream)
+    return C

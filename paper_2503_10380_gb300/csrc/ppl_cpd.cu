@@ -1,0 +1,960 @@
+// libpplcpd: C ABI and the ALS sweep orchestration (host side).
+//
+// One sweep (Optimizing the CP-PPL tensor-network section; Gauss-Seidel
+// order a, b, i, j, each update using the newest factors):
+//   phase A  KR[ij,r] = Ui[i,r] Uj[j,r];  T[r,c,d] = sum_ij tau[ij,cd] KR[ij,r]   (tau^{cd}_r)
+//            mode a:  per r-chunk  W = B.Ub  ->  Y_r = W_r T_r^T  ->  M_a += B . Y   (Eq. foreachr)
+//                     solve: V = Gb.Gi.Gj, Cholesky, U~ = M V^-1, normalise, Ga = Ua^T Ua
+//            mode b:  the same with Ua (new) and T transposed
+//   phase B  per r-chunk  Wa = B.Ua, Wb = B.Ub, S_r = Wa_r^T Wb_r, P[ij,r] += sum_cd tau[ij,cd] S_r[cd]
+//            modes i, j: M_i = sum_j P Uj, solve; M_j = sum_i P Ui (new), solve
+//            fit terms: <R,R~> from M_j, ||R~||^2 from the four Gram matrices (Eq. cp_norm2)
+// Only r-chunks of the X*v*R intermediates exist at any time.
+#include "ppl_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ppl_cpd.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
+
+struct Layout {
+    // offsets (bytes) into the workspace; -1 = absent
+    size_t G[4], V, Linv, Z, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
+    size_t T64, W64, Y64, S64;                       // FP64 form
+    size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S;   // tensor-core form
+    size_t Za, Zb, gov, Gblk, Rblk;
+    size_t total;
+    int rc, na;
+    long long ldv, ldX, ldo2, ldvv;
+};
+
+constexpr int NPART = 2 * 304 + 8;
+constexpr int NSCAL = 64;
+// scalar slots
+constexpr int SC_TOL = 0, SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
+              SC_EXACT = 14;
+
+bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
+    if (o < 1 || v < 1 || X < 1 || R < 1) return false;
+    if ((long long)o * o > (1 << 28) || (long long)v * v > (1 << 29) || (long long)X * v > (1 << 29) || R > (1 << 20))
+        return false;
+    const bool tc = op.precision != PPL_PREC_FP64;
+    L.ldv = rup(v, 8);
+    L.ldX = rup(X, 8);
+    L.ldo2 = rup((long long)o * o, 8);
+    L.ldvv = rup((long long)v * v, 8);
+    int rc = op.r_chunk > 0 ? op.r_chunk : 128;
+    if (rc > 256) rc = 256;
+    if (rc > R) rc = R;
+    if (tc && rc % 16) rc = (int)rup(rc, 16) > 256 ? 256 : (int)rup(rc, 16);
+    if (rc > R) rc = R;
+    L.rc = rc;
+    const long long dim = v > o ? v : o;
+    const long long v3 = (long long)v * v * v;
+    long long na = 32ll * 1024 * 1024 / (v3 + (long long)v * o * o);
+    if (na < 1) na = 1;
+    if (na > v) na = v;
+    L.na = (int)na;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += (size_t)rup((long long)bytes, 256);
+        return at;
+    };
+    const size_t d = sizeof(double);
+    const size_t RR = (size_t)R * R;
+    for (int m = 0; m < 4; ++m) L.G[m] = take(RR * d);
+    L.V = take(RR * d);
+    L.Linv = take((size_t)((R + 31) / 32) * 32 * 32 * d);
+    L.Z = take((size_t)dim * R * d);
+    L.M = take((size_t)dim * R * d);
+    L.P = take((size_t)o * o * R * d);
+    L.scal = take(NSCAL * d);
+    L.partial = take(NPART * d);
+    L.hist = take(4 * d);
+    L.flags = take(64);
+    L.KR64 = take((size_t)R * o * o * d);
+    for (int m = 0; m < 4; ++m) L.Uold[m] = take((size_t)dim * R * d);
+    L.lamold = take((size_t)R * d);
+    for (int m = 0; m < 4; ++m) L.Xc[m] = take(RR * d);
+    L.Za = take((size_t)X * o * R * d);
+    L.Zb = take((size_t)X * o * R * d);
+    L.gov = take((size_t)o * v * o * v * d);
+    L.Gblk = take((size_t)na * v3 * d);
+    L.Rblk = take((size_t)na * v * o * o * d);
+    const size_t none = (size_t)-1;
+    L.T64 = L.W64 = L.Y64 = L.S64 = none;
+    L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
+    if (!tc) {
+        L.T64 = take((size_t)R * v * v * d);
+        L.W64 = take((size_t)rc * X * v * d);
+        L.Y64 = take((size_t)rc * X * v * d);
+        L.S64 = take((size_t)rc * v * v * d);
+    } else {
+        const size_t e = 4;   // bf16 hi + lo, or one fp32
+        L.tauT = take((size_t)v * v * L.ldo2 * e);
+        L.tauN = take((size_t)o * o * L.ldvv * e);
+        L.Bn = take((size_t)X * v * L.ldv * e);
+        L.Bp = take((size_t)v * X * L.ldv * e);
+        L.UopA = take((size_t)R * L.ldv * e);
+        L.UopB = take((size_t)R * L.ldv * e);
+        L.KRT = take((size_t)R * L.ldo2 * e);
+        L.T = take((size_t)R * v * L.ldv * e);
+        L.Tt = take((size_t)R * v * L.ldv * e);
+        L.W = take((size_t)rc * X * L.ldv * e);
+        L.Y = take((size_t)rc * X * L.ldv * e);
+        L.WTa = take((size_t)rc * v * L.ldX * e);
+        L.WTb = take((size_t)rc * v * L.ldX * e);
+        L.S = take((size_t)rc * L.ldvv * e);
+    }
+    L.total = off;
+    return true;
+}
+
+}  // namespace
+
+struct ppl_cpd {
+    int o, v, X, R, n;
+    ppl_cpd_opts opts;
+    cudaStream_t user;   // caller's stream
+    cudaStream_t st;     // internal stream (capturable)
+    cudaEvent_t ev_in, ev_out;
+    const double* B;
+    const double* tau;
+    double* fac;
+    double* U[4];
+    double* lam;
+    char* ws;
+    size_t ws_bytes;
+    Layout L;
+    double normR2;
+    bool have_normR2;
+    long long sweeps;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    bool graph_ready;
+    double last_hist[4];
+    std::string err;
+
+    template <class T>
+    T* at(size_t off) const { return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(ws + off); }
+    double* G(int m) const { return at<double>(L.G[m]); }
+    double* scal() const { return at<double>(L.scal); }
+    unsigned long long* nclamp() const { return at<unsigned long long>(L.flags); }
+    unsigned int* errflag() const { return reinterpret_cast<unsigned int*>(ws + L.flags + 8); }
+    int dim(int m) const { return m < 2 ? v : o; }
+    bool tc() const { return opts.precision != PPL_PREC_FP64; }
+};
+
+namespace {
+
+int fail(ppl_cpd* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_err = buf;
+    return code;
+}
+
+int check_cuda(ppl_cpd* h, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, PPL_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+    return PPL_OK;
+}
+
+// ---- tensor-core helpers ------------------------------------------------------
+
+TcMat mat(void* p, long long plane, int rows, int cols, int batch, long long ld, long long bstride) {
+    TcMat t;
+    t.ptr = p;
+    t.plane_elems = plane;
+    t.rows = rows;
+    t.cols = cols;
+    t.batch = batch;
+    t.ld = ld;
+    t.bstride = bstride;
+    return t;
+}
+
+TcOut out_split(void* p, long long plane, long long sb, int mdiv, long long sm_hi, long long sm_lo, int ndiv,
+                long long sn_hi, long long sn_lo) {
+    TcOut o{};
+    o.kind = EPI_SPLIT;
+    o.out = p;
+    o.plane_elems = plane;
+    o.sb = sb;
+    o.mdiv = mdiv;
+    o.sm_hi = sm_hi;
+    o.sm_lo = sm_lo;
+    o.ndiv = ndiv;
+    o.sn_hi = sn_hi;
+    o.sn_lo = sn_lo;
+    o.alpha = 1.0f;
+    return o;
+}
+
+int auto_ksplit(int M, int N, int bn, int K, int prec) {
+    const int ke = prec == PPL_PREC_BF16X3 ? 64 : 32;
+    const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
+    const long long nkb = (K + ke - 1) / ke;
+    long long ks = (304 + tiles - 1) / tiles;
+    if (ks > nkb) ks = nkb;
+    if (ks < 1) ks = 1;
+    return (int)ks;
+}
+
+int bn_for(int N) {
+    int tiles = (N + 255) / 256;
+    int bn = (N + tiles - 1) / tiles;
+    return (bn + 15) / 16 * 16;
+}
+
+int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
+    g.prec = h->opts.precision;
+    if (g.bn == 0) g.bn = bn_for(g.N);
+    const int r = tc_gemm(g, h->errflag(), h->st);
+    if (r != 0) return fail(h, PPL_ECUDA, "tensor-core GEMM (%s) failed to launch (%d)", what, r);
+    return PPL_OK;
+}
+
+// ---- FP64 pieces shared by both precisions ------------------------------------
+
+void gram(ppl_cpd* h, int m) {
+    G64 g{};
+    const int R = h->R;
+    g.A = h->U[m]; g.am = ix1(1); g.ak = ix1(R);
+    g.B = h->U[m]; g.bn = ix1(1); g.bk = ix1(R);
+    g.C = h->G(m); g.cm = ix1(R); g.cn = ix1(1);
+    g.M = R; g.N = R; g.K = h->dim(m); g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+}
+
+// solve the normal equations of mode m from M (in L.M), update U[m], lam, G[m]
+void solve_mode(ppl_cpd* h, int m) {
+    const int R = h->R, dim = h->dim(m);
+    int oth[3], k = 0;
+    for (int q = 0; q < 4; ++q)
+        if (q != m) oth[k++] = q;
+    double* V = h->at<double>(h->L.V);
+    double* Z = h->at<double>(h->L.Z);
+    hadamard3(h->G(oth[0]), h->G(oth[1]), h->G(oth[2]), R, V, h->scal() + SC_TOL, h->st);
+    cholesky_blocked(V, R, h->at<double>(h->L.Linv), h->scal() + SC_TOL, h->nclamp(), h->st);
+    cudaMemcpyAsync(Z, h->at<double>(h->L.M), (size_t)dim * R * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    chol_solve_right(V, h->at<double>(h->L.Linv), R, Z, dim, h->st);
+    normalise_cols(Z, dim, R, h->U[m], h->lam, h->st);
+    gram(h, m);
+}
+
+// ---- MTTKRP, FP64 form --------------------------------------------------------
+
+void t_fp64(ppl_cpd* h) {
+    const int o = h->o, v = h->v, R = h->R;
+    double* KR = h->at<double>(h->L.KR64);
+    kr_build_f64(h->U[2], h->U[3], o, R, KR, o * o, h->st);
+    G64 g{};
+    g.A = KR; g.am = ix1((long long)o * o); g.ak = ix1(1);
+    g.B = h->tau; g.bn = ix1(1); g.bk = ix1((long long)v * v);
+    g.C = h->at<double>(h->L.T64); g.cm = ix1((long long)v * v); g.cn = ix1(1);
+    g.M = R; g.N = v * v; g.K = o * o; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+}
+
+// W[r][Q][d] = sum_b B[Q][o+b][o+d] U[b][r0+r]
+void w_fp64(ppl_cpd* h, const double* U, int r0, int rcur, double* W) {
+    const int o = h->o, v = h->v, X = h->X, R = h->R, n = h->n;
+    G64 g{};
+    g.A = h->B + (long long)o * n + o; g.am = ix2(v, (long long)n * n, n); g.ak = ix1(1);
+    g.B = U + r0; g.bn = ix1(1); g.bk = ix1(R);
+    g.C = W; g.cm = ix1(1); g.cn = ix1((long long)X * v);
+    g.M = X * v; g.N = rcur; g.K = v; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+}
+
+void mttkrp_ab_fp64(ppl_cpd* h, int mode, double* Mout) {
+    const int o = h->o, v = h->v, X = h->X, R = h->R, n = h->n, rc = h->L.rc;
+    double* T = h->at<double>(h->L.T64);
+    double* W = h->at<double>(h->L.W64);
+    double* Y = h->at<double>(h->L.Y64);
+    cudaMemsetAsync(Mout, 0, (size_t)v * R * sizeof(double), h->st);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rcur = (R - r0 < rc) ? R - r0 : rc;
+        w_fp64(h, mode == 0 ? h->U[1] : h->U[0], r0, rcur, W);
+        G64 y{};
+        y.A = W; y.ab = (long long)X * v; y.am = ix1(v); y.ak = ix1(1);
+        y.B = T + (long long)r0 * v * v; y.bb = (long long)v * v;
+        if (mode == 0) { y.bn = ix1(v); y.bk = ix1(1); }   // T[r][c][d], contract d
+        else           { y.bn = ix1(1); y.bk = ix1(v); }   // T[r][c][d], contract c
+        y.C = Y; y.cb = (long long)X * v; y.cm = ix1(v); y.cn = ix1(1);
+        y.M = X; y.N = v; y.K = v; y.batch = rcur; y.ksplit = 1; y.alpha = 1.0;
+        gemm64(y, h->st);
+        G64 m{};
+        m.A = h->B + (long long)o * n + o; m.am = ix1(n); m.ak = ix2(v, (long long)n * n, 1);
+        m.B = Y; m.bn = ix1((long long)X * v); m.bk = ix1(1);
+        m.C = Mout + r0; m.cm = ix1(R); m.cn = ix1(1);
+        m.M = v; m.N = rcur; m.K = X * v; m.batch = 1; m.alpha = 1.0; m.atomic = 1;
+        const long long tiles = (long long)((v + 63) / 64) * ((rcur + 63) / 64);
+        long long ks = (608 + tiles - 1) / tiles;
+        if (ks > (X * (long long)v) / 64) ks = (X * (long long)v) / 64;
+        m.ksplit = ks < 1 ? 1 : (int)ks;
+        gemm64(m, h->st);
+    }
+}
+
+void p_fp64(ppl_cpd* h) {
+    const int o = h->o, v = h->v, X = h->X, R = h->R, rc = h->L.rc;
+    double* Wa = h->at<double>(h->L.W64);
+    double* Wb = h->at<double>(h->L.Y64);
+    double* S = h->at<double>(h->L.S64);
+    double* P = h->at<double>(h->L.P);
+    cudaMemsetAsync(P, 0, (size_t)o * o * R * sizeof(double), h->st);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rcur = (R - r0 < rc) ? R - r0 : rc;
+        w_fp64(h, h->U[0], r0, rcur, Wa);
+        w_fp64(h, h->U[1], r0, rcur, Wb);
+        G64 s{};
+        s.A = Wa; s.ab = (long long)X * v; s.am = ix1(1); s.ak = ix1(v);
+        s.B = Wb; s.bb = (long long)X * v; s.bn = ix1(1); s.bk = ix1(v);
+        s.C = S; s.cb = (long long)v * v; s.cm = ix1(v); s.cn = ix1(1);
+        s.M = v; s.N = v; s.K = X; s.batch = rcur; s.ksplit = 1; s.alpha = 1.0;
+        gemm64(s, h->st);
+        G64 p{};
+        p.A = h->tau; p.am = ix1((long long)v * v); p.ak = ix1(1);
+        p.B = S; p.bn = ix1((long long)v * v); p.bk = ix1(1);
+        p.C = P + r0; p.cm = ix1(R); p.cn = ix1(1);
+        p.M = o * o; p.N = rcur; p.K = v * v; p.batch = 1; p.alpha = 1.0; p.atomic = 1;
+        const long long tiles = (long long)((o * o + 63) / 64) * ((rcur + 63) / 64);
+        long long ks = (608 + tiles - 1) / tiles;
+        if (ks > (long long)v * v / 64) ks = (long long)v * v / 64;
+        p.ksplit = ks < 1 ? 1 : (int)ks;
+        gemm64(p, h->st);
+    }
+}
+
+// ---- MTTKRP, tensor-core form ---------------------------------------------------
+
+void* opb(ppl_cpd* h, size_t off) { return h->ws + off; }
+
+int uop(ppl_cpd* h, int m, size_t dst) {
+    SplitSrc s{};
+    s.src = h->U[m];
+    s.rmap = ix1(1);
+    s.cmap = ix1(h->R);
+    const long long plane = (long long)h->R * h->L.ldv;
+    split_to_operand(h->opts.precision, s, h->R, h->dim(m), 1, opb(h, dst), plane, h->L.ldv, 0, h->st);
+    return PPL_OK;
+}
+
+int t_tc(ppl_cpd* h) {
+    const int o = h->o, v = h->v, R = h->R;
+    const long long ldv = h->L.ldv, ldo2 = h->L.ldo2;
+    double* KR = h->at<double>(h->L.KR64);
+    kr_build_f64(h->U[2], h->U[3], o, R, KR, o * o, h->st);
+    SplitSrc s{};
+    s.src = KR;
+    s.rmap = ix1((long long)o * o);
+    s.cmap = ix1(1);
+    const long long pKRT = (long long)R * ldo2;
+    split_to_operand(h->opts.precision, s, R, o * o, 1, opb(h, h->L.KRT), pKRT, ldo2, 0, h->st);
+    const long long pT = (long long)R * v * ldv;
+    TcGemm g{};
+    g.A = mat(opb(h, h->L.tauT), (long long)v * v * ldo2, v * v, o * o, 1, ldo2, 0);
+    g.B = mat(opb(h, h->L.KRT), pKRT, R, o * o, 1, ldo2, 0);
+    g.M = v * v; g.N = R; g.K = o * o; g.batch = 1; g.ksplit = 1;
+    // T[r][c][d]: m = c*v + d
+    g.out = out_split(opb(h, h->L.T), pT, 0, v, ldv, 1, 0, 0, (long long)v * ldv);
+    int rc = run_tc(h, g, "T");
+    if (rc) return rc;
+    // T transposed: Tt[r][d][c] = T[r][c][d], produced by a second epilogue pass of the same GEMM
+    TcGemm gt = g;
+    gt.out = out_split(opb(h, h->L.Tt), pT, 0, v, 1, ldv, 0, 0, (long long)v * ldv);
+    return run_tc(h, gt, "Tt");
+}
+
+int chain_tc(ppl_cpd* h, int mode, double* Mout) {
+    const int v = h->v, X = h->X, R = h->R, rc = h->L.rc;
+    const long long ldv = h->L.ldv;
+    const long long pB = (long long)X * v * ldv;          // Bn / Bp plane
+    const long long pU = (long long)R * ldv;
+    const long long pT = (long long)R * v * ldv;
+    const long long pW = (long long)rc * X * ldv;
+    cudaMemsetAsync(Mout, 0, (size_t)v * R * sizeof(double), h->st);
+    uop(h, mode == 0 ? 1 : 0, h->L.UopA);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rcur = (R - r0 < rc) ? R - r0 : rc;
+        // W[r][Q][d] = sum_b B[Q][d][b] U[b][r0+r]
+        TcGemm g1{};
+        g1.A = mat(opb(h, h->L.Bn), pB, X * v, v, 1, ldv, 0);
+        g1.B = mat(opb(h, h->L.UopA), pU, R, v, 1, ldv, 0);
+        g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
+        g1.out = out_split(opb(h, h->L.W), pW, 0, v, ldv, 1, 0, 0, (long long)X * ldv);
+        int e = run_tc(h, g1, "W");
+        if (e) return e;
+        // Y[r][Q][c] = sum_d T[r][c][d] W[r][Q][d]   (mode b: Tt, contracting c)
+        TcGemm g2{};
+        g2.A = mat(opb(h, mode == 0 ? h->L.T : h->L.Tt), pT, v, v, R, ldv, (long long)v * ldv);
+        g2.a_b0 = r0; g2.a_bstep = 1;
+        g2.B = mat(opb(h, h->L.W), pW, X, v, rc, ldv, (long long)X * ldv);
+        g2.b_b0 = 0; g2.b_bstep = 1;
+        g2.M = v; g2.N = X; g2.K = v; g2.batch = rcur; g2.ksplit = 1;
+        g2.out = out_split(opb(h, h->L.Y), pW, (long long)X * ldv, 0, 0, 1, 0, 0, ldv);
+        e = run_tc(h, g2, "Y");
+        if (e) return e;
+        // M[a][r0+r] += sum_{Q,c} B[Q][a][c] Y[r][Q][c]
+        TcGemm g3{};
+        g3.A = mat(opb(h, h->L.Bp), pB, v, (int)(X * ldv), 1, X * ldv, 0);
+        g3.B = mat(opb(h, h->L.Y), pW, rc, (int)(X * ldv), 1, X * ldv, 0);
+        g3.M = v; g3.N = rcur; g3.K = (int)(X * ldv); g3.batch = 1;
+        g3.bn = bn_for(rcur);
+        g3.ksplit = auto_ksplit(v, rcur, g3.bn, g3.K, h->opts.precision);
+        g3.out = TcOut{};
+        g3.out.kind = EPI_ATOMIC_F64; g3.out.out = Mout + r0; g3.out.sm_lo = R; g3.out.sn_lo = 1; g3.out.alpha = 1.0f;
+        e = run_tc(h, g3, "M");
+        if (e) return e;
+    }
+    return PPL_OK;
+}
+
+int p_tc(ppl_cpd* h) {
+    const int o = h->o, v = h->v, X = h->X, R = h->R, rc = h->L.rc;
+    const long long ldv = h->L.ldv, ldX = h->L.ldX, ldvv = h->L.ldvv;
+    const long long pB = (long long)X * v * ldv;
+    const long long pU = (long long)R * ldv;
+    const long long pWT = (long long)rc * v * ldX;
+    const long long pS = (long long)rc * ldvv;
+    double* P = h->at<double>(h->L.P);
+    cudaMemsetAsync(P, 0, (size_t)o * o * R * sizeof(double), h->st);
+    uop(h, 0, h->L.UopA);
+    uop(h, 1, h->L.UopB);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rcur = (R - r0 < rc) ? R - r0 : rc;
+        for (int w = 0; w < 2; ++w) {
+            // WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; rows (c,Q) of Bp
+            TcGemm g1{};
+            g1.A = mat(opb(h, h->L.Bp), pB, v * X, v, 1, ldv, 0);
+            g1.B = mat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, ldv, 0);
+            g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
+            g1.out = out_split(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, ldX, 1, 0, 0, (long long)v * ldX);
+            int e = run_tc(h, g1, "WT");
+            if (e) return e;
+        }
+        // S[r][c*v + d] = sum_Q WTa[r][c][Q] WTb[r][d][Q]
+        TcGemm gs{};
+        gs.A = mat(opb(h, h->L.WTb), pWT, v, X, rc, ldX, (long long)v * ldX);
+        gs.B = mat(opb(h, h->L.WTa), pWT, v, X, rc, ldX, (long long)v * ldX);
+        gs.a_bstep = 1; gs.b_bstep = 1;
+        gs.M = v; gs.N = v; gs.K = X; gs.batch = rcur; gs.ksplit = 1;
+        gs.out = out_split(opb(h, h->L.S), pS, ldvv, 0, 0, 1, 0, 0, v);
+        int e = run_tc(h, gs, "S");
+        if (e) return e;
+        // P[ij][r0+r] += sum_cd tau[ij][cd] S[r][cd]
+        TcGemm gp{};
+        gp.A = mat(opb(h, h->L.tauN), (long long)o * o * ldvv, o * o, v * v, 1, ldvv, 0);
+        gp.B = mat(opb(h, h->L.S), pS, rc, v * v, 1, ldvv, 0);
+        gp.M = o * o; gp.N = rcur; gp.K = v * v; gp.batch = 1;
+        gp.bn = bn_for(rcur);
+        gp.ksplit = auto_ksplit(o * o, rcur, gp.bn, gp.K, h->opts.precision);
+        gp.out = TcOut{};
+        gp.out.kind = EPI_ATOMIC_F64; gp.out.out = P + r0; gp.out.sm_lo = R; gp.out.sn_lo = 1; gp.out.alpha = 1.0f;
+        e = run_tc(h, gp, "P");
+        if (e) return e;
+    }
+    return PPL_OK;
+}
+
+// operand copies of tau and B (once per tau / B)
+int prepare_operands(ppl_cpd* h, bool tau_only) {
+    if (!h->tc()) return PPL_OK;
+    const int o = h->o, v = h->v, X = h->X, n = h->n, prec = h->opts.precision;
+    const long long ldv = h->L.ldv, ldo2 = h->L.ldo2, ldvv = h->L.ldvv;
+    SplitSrc s{};
+    s.src = h->tau; s.rmap = ix1(1); s.cmap = ix1((long long)v * v);
+    split_to_operand(prec, s, v * v, o * o, 1, opb(h, h->L.tauT), (long long)v * v * ldo2, ldo2, 0, h->st);
+    s.rmap = ix1((long long)v * v); s.cmap = ix1(1);
+    split_to_operand(prec, s, o * o, v * v, 1, opb(h, h->L.tauN), (long long)o * o * ldvv, ldvv, 0, h->st);
+    if (tau_only) return PPL_OK;
+    const long long pB = (long long)X * v * ldv;
+    s.src = h->B + (long long)o * n + o; s.rmap = ix2(v, (long long)n * n, n); s.cmap = ix1(1);
+    split_to_operand(prec, s, X * v, v, 1, opb(h, h->L.Bn), pB, ldv, 0, h->st);
+    s.rmap = ix2(X, n, (long long)n * n);
+    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.Bp), pB, ldv, 0, h->st);
+    // scratch whose padding must read as zero
+    zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * ldv * 4, h->st);
+    zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * ldvv * 4, h->st);
+    zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * ldv * 4, h->st);
+    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * h->L.ldX * 4, h->st);
+    zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * h->L.ldX * 4, h->st);
+    return PPL_OK;
+}
+
+int mttkrp_into(ppl_cpd* h, int mode, double* Mout) {
+    const int o = h->o, R = h->R;
+    if (mode < 2) {
+        if (h->tc()) {
+            int e = t_tc(h);
+            if (e) return e;
+            return chain_tc(h, mode, Mout);
+        }
+        t_fp64(h);
+        mttkrp_ab_fp64(h, mode, Mout);
+        return PPL_OK;
+    }
+    if (h->tc()) {
+        int e = p_tc(h);
+        if (e) return e;
+    } else {
+        p_fp64(h);
+    }
+    occ_mttkrp(h->at<double>(h->L.P), R, mode == 2 ? h->U[3] : h->U[2], o, R, mode == 2 ? 0 : 1, Mout, h->st);
+    return PPL_OK;
+}
+
+// cross Gram X_m = U_m^T Uold_m
+void cross_gram(ppl_cpd* h, int m) {
+    G64 g{};
+    const int R = h->R;
+    g.A = h->U[m]; g.am = ix1(1); g.ak = ix1(R);
+    g.B = h->at<double>(h->L.Uold[m]); g.bn = ix1(1); g.bk = ix1(R);
+    g.C = h->at<double>(h->L.Xc[m]); g.cm = ix1(R); g.cn = ix1(1);
+    g.M = R; g.N = R; g.K = h->dim(m); g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+}
+
+int sweep_body(ppl_cpd* h) {
+    const int o = h->o, v = h->v, R = h->R;
+    double* M = h->at<double>(h->L.M);
+    double* hist = h->at<double>(h->L.hist);
+    if (h->opts.want_eta) {
+        for (int m = 0; m < 4; ++m)
+            cudaMemcpyAsync(h->at<double>(h->L.Uold[m]), h->U[m], (size_t)h->dim(m) * R * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->st);
+        cudaMemcpyAsync(h->at<double>(h->L.lamold), h->lam, (size_t)R * sizeof(double), cudaMemcpyDeviceToDevice,
+                        h->st);
+    }
+    int e;
+    if (h->tc()) {
+        if ((e = t_tc(h))) return e;
+        if ((e = chain_tc(h, 0, M))) return e;
+        solve_mode(h, 0);
+        if ((e = chain_tc(h, 1, M))) return e;
+        solve_mode(h, 1);
+        if ((e = p_tc(h))) return e;
+    } else {
+        t_fp64(h);
+        mttkrp_ab_fp64(h, 0, M);
+        solve_mode(h, 0);
+        mttkrp_ab_fp64(h, 1, M);
+        solve_mode(h, 1);
+        p_fp64(h);
+    }
+    double* P = h->at<double>(h->L.P);
+    occ_mttkrp(P, R, h->U[3], o, R, 0, M, h->st);
+    solve_mode(h, 2);
+    occ_mttkrp(P, R, h->U[2], o, R, 1, M, h->st);
+    solve_mode(h, 3);
+    double* sc = h->scal();
+    fit_terms(M, h->U[3], h->lam, o, R, h->G(0), h->G(1), h->G(2), h->G(3), h->at<double>(h->L.partial),
+              sc + SC_TERMS, h->st);
+    finish_fit(sc + SC_TERMS, sc + SC_NORMR2, hist, h->st);
+    if (h->opts.want_eta) {
+        for (int m = 0; m < 4; ++m) cross_gram(h, m);
+        eta_terms(h->at<double>(h->L.Xc[0]), h->at<double>(h->L.Xc[1]), h->at<double>(h->L.Xc[2]),
+                  h->at<double>(h->L.Xc[3]), h->lam, h->at<double>(h->L.lamold), R, h->at<double>(h->L.partial),
+                  sc + SC_CROSS, h->st);
+        finish_eta(sc + SC_CROSS, sc + SC_TERMS + 1, sc + SC_NORM2_PREV, hist, h->st);
+        cudaMemcpyAsync(sc + SC_NORM2_PREV, sc + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    }
+    (void)v;
+    return check_cuda(h, "sweep");
+}
+
+int enter(ppl_cpd* h) {
+    cudaEventRecord(h->ev_in, h->user);
+    cudaStreamWaitEvent(h->st, h->ev_in, 0);
+    return check_cuda(h, "stream order");
+}
+
+int leave(ppl_cpd* h) {
+    cudaEventRecord(h->ev_out, h->st);
+    cudaStreamWaitEvent(h->user, h->ev_out, 0);
+    return check_cuda(h, "stream order");
+}
+
+int sync_and_check(ppl_cpd* h) {
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return fail(h, PPL_ECUDA, "stream synchronise: %s", cudaGetErrorString(e));
+    unsigned int flag = 0;
+    cudaMemcpy(&flag, h->errflag(), sizeof flag, cudaMemcpyDeviceToHost);
+    if (flag) {
+        cudaMemset(h->errflag(), 0, sizeof flag);
+        return fail(h, PPL_ETIMEOUT, "a bounded device wait expired (flags 0x%x)", flag);
+    }
+    return PPL_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+void ppl_cpd_default_opts(ppl_cpd_opts* opts) {
+    if (!opts) return;
+    memset(opts, 0, sizeof *opts);
+    opts->precision = PPL_PREC_BF16X3;
+    opts->r_chunk = 0;
+    opts->use_graph = 1;
+    opts->want_eta = 0;
+}
+
+int ppl_cpd_workspace_size(int o, int v, int X, int R, const ppl_cpd_opts* opts, size_t* bytes) {
+    ppl_cpd_opts op;
+    ppl_cpd_default_opts(&op);
+    if (opts) op = *opts;
+    if (!bytes) return fail(nullptr, PPL_EINVAL, "bytes is NULL");
+    if (op.precision < 0 || op.precision > 2) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
+    Layout L;
+    if (!plan(o, v, X, R, op, L)) return fail(nullptr, PPL_EINVAL, "sizes out of range (o=%d v=%d X=%d R=%d)", o, v, X, R);
+    *bytes = L.total;
+    return PPL_OK;
+}
+
+int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, const double* tau, double* factors,
+                 void* workspace, size_t ws_bytes, const ppl_cpd_opts* opts, void* stream) {
+    if (!hp) return fail(nullptr, PPL_EINVAL, "handle pointer is NULL");
+    *hp = nullptr;
+    ppl_cpd_opts op;
+    ppl_cpd_default_opts(&op);
+    if (opts) op = *opts;
+    if (op.precision < 0 || op.precision > 2) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
+    if (!B || !tau || !factors || !workspace) return fail(nullptr, PPL_EINVAL, "NULL device pointer");
+    if (((uintptr_t)workspace) % 256) return fail(nullptr, PPL_EINVAL, "workspace not 256-byte aligned");
+    Layout L;
+    if (!plan(o, v, X, R, op, L)) return fail(nullptr, PPL_EINVAL, "sizes out of range (o=%d v=%d X=%d R=%d)", o, v, X, R);
+    if (ws_bytes < L.total)
+        return fail(nullptr, PPL_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    if (op.precision != PPL_PREC_FP64 && tc_init_driver() != 0)
+        return fail(nullptr, PPL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    ppl_cpd* h = new (std::nothrow) ppl_cpd();
+    if (!h) return fail(nullptr, PPL_EINVAL, "out of host memory");
+    h->o = o; h->v = v; h->X = X; h->R = R; h->n = o + v;
+    h->opts = op;
+    h->user = (cudaStream_t)stream;
+    h->B = B; h->tau = tau; h->fac = factors;
+    h->U[0] = factors;
+    h->U[1] = factors + (size_t)v * R;
+    h->U[2] = factors + (size_t)2 * v * R;
+    h->U[3] = factors + (size_t)2 * v * R + (size_t)o * R;
+    h->lam = factors + (size_t)2 * v * R + (size_t)2 * o * R;
+    h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
+    h->L = L;
+    h->normR2 = 0.0; h->have_normR2 = false; h->sweeps = 0;
+    h->graph = nullptr; h->gexec = nullptr; h->graph_ready = false;
+    for (double& x : h->last_hist) x = nan("");
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, PPL_ECUDA, "could not create the internal stream/events");
+    }
+    int e = enter(h);
+    if (!e) {
+        cudaMemsetAsync(h->ws + L.scal, 0, NSCAL * sizeof(double), h->st);
+        cudaMemsetAsync(h->ws + L.flags, 0, 64, h->st);
+        fill_f64(h->lam, (size_t)R, 1.0, h->st);
+        for (int m = 0; m < 4; ++m) gram(h, m);
+        // ||R~_0||^2 of the initial guess (eta's first denominator)
+        fit_terms(h->at<double>(h->L.M), h->U[0], h->lam, 0, R, h->G(0), h->G(1), h->G(2), h->G(3),
+                  h->at<double>(h->L.partial), h->scal() + SC_TERMS, h->st);
+        cudaMemcpyAsync(h->scal() + SC_NORM2_PREV, h->scal() + SC_TERMS + 1, sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->st);
+        e = prepare_operands(h, false);
+    }
+    if (!e) e = check_cuda(h, "init");
+    if (!e) e = leave(h);
+    if (e) {
+        g_err = h->err;
+        cudaStreamDestroy(h->st);
+        cudaEventDestroy(h->ev_in);
+        cudaEventDestroy(h->ev_out);
+        delete h;
+        return e;
+    }
+    *hp = h;
+    return PPL_OK;
+}
+
+int ppl_cpd_mttkrp(ppl_cpd* h, int mode, double* M_out) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (mode < 0 || mode > 3) return fail(h, PPL_EINVAL, "mode %d out of range", mode);
+    if (!M_out) return fail(h, PPL_EINVAL, "M_out is NULL");
+    int e = enter(h);
+    if (!e) e = mttkrp_into(h, mode, M_out);
+    if (!e) e = check_cuda(h, "mttkrp");
+    if (!e) e = sync_and_check(h);
+    leave(h);
+    return e;
+}
+
+int ppl_cpd_sweep(ppl_cpd* h, int nsweeps, double* fit_hist) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (nsweeps < 0) return fail(h, PPL_EINVAL, "nsweeps < 0");
+    if (nsweeps == 0) return PPL_OK;
+    int e = enter(h);
+    if (e) return e;
+    double* hist = h->at<double>(h->L.hist);
+    double host_hist[4];
+    for (int k = 0; k < nsweeps; ++k) {
+        if (h->opts.use_graph) {
+            if (!h->graph_ready) {
+                cudaError_t ce = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+                if (ce != cudaSuccess) return fail(h, PPL_ECUDA, "begin capture: %s", cudaGetErrorString(ce));
+                int be = sweep_body(h);
+                cudaGraph_t gr = nullptr;
+                ce = cudaStreamEndCapture(h->st, &gr);
+                if (be) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return be;
+                }
+                if (ce != cudaSuccess) return fail(h, PPL_ECUDA, "end capture: %s", cudaGetErrorString(ce));
+                ce = cudaGraphInstantiate(&h->gexec, gr, 0);
+                if (ce != cudaSuccess) {
+                    cudaGraphDestroy(gr);
+                    return fail(h, PPL_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+                }
+                h->graph = gr;
+                h->graph_ready = true;
+            }
+            cudaGraphLaunch(h->gexec, h->st);
+        } else {
+            e = sweep_body(h);
+            if (e) return e;
+        }
+        if (fit_hist || k == nsweeps - 1) {
+            e = sync_and_check(h);
+            if (e) { leave(h); return e; }
+            cudaMemcpy(host_hist, hist, sizeof host_hist, cudaMemcpyDeviceToHost);
+            if (fit_hist) fit_hist[k] = host_hist[0];
+            for (int q = 0; q < 4; ++q) h->last_hist[q] = host_hist[q];
+        }
+        h->sweeps++;
+    }
+    e = check_cuda(h, "sweep");
+    leave(h);
+    return e;
+}
+
+int ppl_cpd_set_normR2(ppl_cpd* h, double normR2) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (!(normR2 > 0.0)) return fail(h, PPL_EINVAL, "normR2 must be positive");
+    h->normR2 = normR2;
+    h->have_normR2 = true;
+    int e = enter(h);
+    if (e) return e;
+    cudaMemcpyAsync(h->scal() + SC_NORMR2, &h->normR2, sizeof(double), cudaMemcpyHostToDevice, h->st);
+    e = sync_and_check(h);
+    leave(h);
+    return e;
+}
+
+int ppl_cpd_fit(ppl_cpd* h, double* fit) {
+    if (!h || !fit) return fail(h, PPL_EINVAL, "NULL argument");
+    if (!h->have_normR2) return fail(h, PPL_ENOTREADY, "||R||^2 unknown: call ppl_exact_contract or ppl_cpd_set_normR2");
+    if (h->sweeps == 0) return fail(h, PPL_ENOTREADY, "no sweep has run");
+    const double inner = h->last_hist[1], norm2 = h->last_hist[2];
+    *fit = 1.0 - sqrt(fmax(h->normR2 - 2.0 * inner + norm2, 0.0)) / sqrt(h->normR2);
+    return PPL_OK;
+}
+
+int ppl_cpd_energy(ppl_cpd* h, double* E_cp) {
+    if (!h || !E_cp) return fail(h, PPL_EINVAL, "NULL argument");
+    const int o = h->o, v = h->v, X = h->X, R = h->R, n = h->n;
+    int e = enter(h);
+    if (e) return e;
+    double* Z[2] = {h->at<double>(h->L.Za), h->at<double>(h->L.Zb)};
+    for (int w = 0; w < 2; ++w) {
+        G64 g{};
+        g.A = h->B + o; g.ab = (long long)n * n; g.am = ix1(n); g.ak = ix1(1);
+        g.B = h->U[w]; g.bn = ix1(1); g.bk = ix1(R);
+        g.C = Z[w]; g.cb = (long long)o * R; g.cm = ix1(R); g.cn = ix1(1);
+        g.M = o; g.N = R; g.K = v; g.batch = X; g.ksplit = 1; g.alpha = 1.0;
+        gemm64(g, h->st);
+    }
+    energy_reduce(Z[0], Z[1], h->U[2], h->U[3], h->lam, X, o, R, h->at<double>(h->L.partial),
+                  h->scal() + SC_ENERGY, h->st);
+    e = check_cuda(h, "energy");
+    if (!e) e = sync_and_check(h);
+    if (!e) cudaMemcpy(E_cp, h->scal() + SC_ENERGY, sizeof(double), cudaMemcpyDeviceToHost);
+    leave(h);
+    return e ? e : check_cuda(h, "energy");
+}
+
+int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_out) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    const int o = h->o, v = h->v, X = h->X, n = h->n, na = h->L.na;
+    int e = enter(h);
+    if (e) return e;
+    double* gov = h->at<double>(h->L.gov);
+    double* Gb = h->at<double>(h->L.Gblk);
+    double* Rb = h->at<double>(h->L.Rblk);
+    double* acc = h->scal() + SC_EXACT;
+    cudaMemsetAsync(acc, 0, 2 * sizeof(double), h->st);
+    // g[i][a][j][b] = sum_Q B[Q][i][o+a] B[Q][j][o+b]
+    G64 g{};
+    g.A = h->B + o; g.am = ix2(v, n, 1); g.ak = ix1((long long)n * n);
+    g.B = h->B + o; g.bn = ix2(v, n, 1); g.bk = ix1((long long)n * n);
+    g.C = gov; g.cm = ix1((long long)o * v); g.cn = ix1(1);
+    g.M = o * v; g.N = o * v; g.K = X; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+    const long long v3 = (long long)v * v * v, vo2 = (long long)v * o * o;
+    for (int a0 = 0; a0 < v; a0 += na) {
+        const int nb = (v - a0 < na) ? v - a0 : na;
+        // G_a[c][b*v+d] = sum_Q B[Q][o+a][o+c] B[Q][o+b][o+d]
+        G64 q{};
+        q.A = h->B + (long long)(o + a0) * n + o; q.ab = n; q.am = ix1(1); q.ak = ix1((long long)n * n);
+        q.B = h->B + (long long)o * n + o; q.bb = 0; q.bn = ix2(v, n, 1); q.bk = ix1((long long)n * n);
+        q.C = Gb; q.cb = v3; q.cm = ix1((long long)v * v); q.cn = ix1(1);
+        q.M = v; q.N = v * v; q.K = X; q.batch = nb; q.ksplit = 1; q.alpha = 1.0;
+        gemm64(q, h->st);
+        // R[a][b][ij] = sum_{c,d} G_a[c][b][d] tau[ij][c][d]
+        double* Rdst = R_out ? R_out + (long long)a0 * vo2 : Rb;
+        G64 r{};
+        r.A = Gb; r.ab = v3; r.am = ix1(v); r.ak = ix2(v, (long long)v * v, 1);
+        r.B = h->tau; r.bb = 0; r.bn = ix1((long long)v * v); r.bk = ix1(1);
+        r.C = Rdst; r.cb = vo2; r.cm = ix1((long long)o * o); r.cn = ix1(1);
+        r.M = v; r.N = o * o; r.K = v * v; r.batch = nb; r.ksplit = 1; r.alpha = 1.0;
+        gemm64(r, h->st);
+        exact_reduce(Rdst, a0, nb, v, o, gov, h->at<double>(h->L.partial), acc, h->st);
+    }
+    e = check_cuda(h, "exact_contract");
+    if (!e) e = sync_and_check(h);
+    double res[2] = {0, 0};
+    if (!e) cudaMemcpy(res, acc, sizeof res, cudaMemcpyDeviceToHost);
+    leave(h);
+    if (e) return e;
+    if (normR2) *normR2 = res[0];
+    if (E_exact) *E_exact = res[1];
+    if (res[0] > 0.0) return ppl_cpd_set_normR2(h, res[0]);
+    return PPL_OK;
+}
+
+int ppl_cpd_set_tau(ppl_cpd* h, const double* tau) {
+    if (!h || !tau) return fail(h, PPL_EINVAL, "NULL argument");
+    h->tau = tau;
+    h->have_normR2 = false;
+    h->normR2 = 0.0;
+    int e = enter(h);
+    if (e) return e;
+    cudaMemsetAsync(h->scal() + SC_NORMR2, 0, sizeof(double), h->st);
+    e = prepare_operands(h, true);
+    if (!e) e = check_cuda(h, "set_tau");
+    if (!e) e = sync_and_check(h);
+    leave(h);
+    // the FP64 form reads tau through its pointer, which a captured graph has baked in
+    if (h->graph_ready) {
+        cudaGraphExecDestroy(h->gexec);
+        cudaGraphDestroy(h->graph);
+        h->gexec = nullptr;
+        h->graph = nullptr;
+        h->graph_ready = false;
+    }
+    return e;
+}
+
+int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
+    if (!h || !s) return fail(h, PPL_EINVAL, "NULL argument");
+    unsigned long long nc = 0;
+    cudaStreamSynchronize(h->st);
+    cudaMemcpy(&nc, h->nclamp(), sizeof nc, cudaMemcpyDeviceToHost);
+    s->sweeps = h->sweeps;
+    s->clamped_pivots = (long long)nc;
+    s->timeouts = 0;
+    s->last_fit = h->have_normR2 ? h->last_hist[0] : nan("");
+    s->last_inner = h->last_hist[1];
+    s->last_norm2 = h->last_hist[2];
+    s->last_eta = h->opts.want_eta ? h->last_hist[3] : nan("");
+    const double o = h->o, v = h->v, X = h->X, R = h->R;
+    s->flops_per_sweep = 4.0 * o * o * v * v * R + 16.0 * X * v * v * R;
+    return check_cuda(h, "stats");
+}
+
+const char* ppl_last_error(const ppl_cpd* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int ppl_cpd_destroy(ppl_cpd* h) {
+    if (!h) return PPL_OK;
+    cudaStreamSynchronize(h->st);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    cudaStreamDestroy(h->st);
+    cudaEventDestroy(h->ev_in);
+    cudaEventDestroy(h->ev_out);
+    delete h;
+    return PPL_OK;
+}
+
+int ppl_tc_gemm_workspace_size(int M, int N, int K, int precision, size_t* bytes) {
+    if (!bytes || M < 1 || N < 1 || K < 1 || (precision != PPL_PREC_BF16X3 && precision != PPL_PREC_TF32))
+        return fail(nullptr, PPL_EINVAL, "bad arguments");
+    const long long ld = rup(K, 8);
+    *bytes = (size_t)rup((long long)M * ld * 4, 256) + (size_t)rup((long long)N * ld * 4, 256) + 256;
+    return PPL_OK;
+}
+
+int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float* B, float* C, void* workspace,
+                size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int e = ppl_tc_gemm_workspace_size(M, N, K, precision, &need);
+    if (e) return e;
+    if (!A || !B || !C || !workspace) return fail(nullptr, PPL_EINVAL, "NULL device pointer");
+    if (ws_bytes < need) return fail(nullptr, PPL_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    if (((uintptr_t)workspace) % 256) return fail(nullptr, PPL_EINVAL, "workspace not 256-byte aligned");
+    if (tc_init_driver() != 0) return fail(nullptr, PPL_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long ld = rup(K, 8);
+    char* w = (char*)workspace;
+    void* Aop = w;
+    void* Bop = w + rup((long long)M * ld * 4, 256);
+    unsigned int* flag = (unsigned int*)(w + rup((long long)M * ld * 4, 256) + rup((long long)N * ld * 4, 256));
+    cudaMemsetAsync(flag, 0, sizeof(unsigned int), s);
+    SplitSrc sa{};
+    sa.src32 = A; sa.rmap = ix1(K); sa.cmap = ix1(1);
+    split_to_operand(precision, sa, M, K, 1, Aop, (long long)M * ld, ld, 0, s);
+    SplitSrc sb{};
+    sb.src32 = B; sb.rmap = ix1(K); sb.cmap = ix1(1);
+    split_to_operand(precision, sb, N, K, 1, Bop, (long long)N * ld, ld, 0, s);
+    TcGemm g{};
+    g.prec = precision;
+    g.A = mat(Aop, (long long)M * ld, M, K, 1, ld, 0);
+    g.B = mat(Bop, (long long)N * ld, N, K, 1, ld, 0);
+    g.M = M; g.N = N; g.K = K; g.batch = 1; g.ksplit = 1;
+    g.out = TcOut{};
+    g.out.kind = EPI_F32; g.out.out = C; g.out.sm_lo = N; g.out.sn_lo = 1; g.out.alpha = 1.0f;
+    g.bn = bn_for(N);
+    int r = tc_gemm(g, flag, s);
+    if (r) return fail(nullptr, PPL_ECUDA, "tensor-core GEMM launch failed (%d)", r);
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "%s", cudaGetErrorString(ce));
+    unsigned int f = 0;
+    cudaMemcpy(&f, flag, sizeof f, cudaMemcpyDeviceToHost);
+    if (f) return fail(nullptr, PPL_ETIMEOUT, "a bounded device wait expired (flags 0x%x)", f);
+    return PPL_OK;
+}
+
+}  // extern "C"

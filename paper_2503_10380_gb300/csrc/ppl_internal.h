@@ -1,0 +1,105 @@
+// Internal interfaces shared by the translation units of libpplcpd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+// Index map i -> (i / div) * hi + (i % div) * lo.  With div >= 2^30 it is a
+// plain stride.  Lets one strided kernel read the flattened compound indices
+// of the method ((Q,c), (c,d), (i,j), ...) straight out of B and tau.
+struct Idx2 {
+    long long hi, lo;
+    int div;
+};
+static inline Idx2 ix1(long long stride) { return Idx2{0, stride, 1 << 30}; }
+static inline Idx2 ix2(int div, long long hi, long long lo) { return Idx2{hi, lo, div}; }
+
+// C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (+ beta * C), FP64.
+struct G64 {
+    const double* A; Idx2 am, ak; long long ab;
+    const double* B; Idx2 bn, bk; long long bb;
+    double* C; Idx2 cm, cn; long long cb;
+    int M, N, K, batch, ksplit;
+    double alpha, beta;
+    int atomic;   // 1: atomicAdd(alpha * acc) into C (split-K); beta ignored
+    int lower;    // 1: skip tiles whose columns all lie above the diagonal (n > m)
+};
+void gemm64(const G64& g, cudaStream_t s);
+
+// ---- small FP64 kernels (ppl_fp64.cu) -------------------------------------
+// KR[r][i*o+j] = Ui[i][r] * Uj[j][r]   (FP64, [R][ld])
+void kr_build_f64(const double* Ui, const double* Uj, int o, int R, double* KR, int ld, cudaStream_t s);
+// V = G1 .* G2 .* G3 (R x R); tol[0] = max(2^-52 R max_k V_kk, 1e-300)
+void hadamard3(const double* G1, const double* G2, const double* G3, int R, double* V, double* tol, cudaStream_t s);
+// lower Cholesky of V in place, blocked (nb = 32); block inverses to Linv [nt][32][32];
+// pivots not above *tol are clamped and counted in *nclamp
+void cholesky_blocked(double* V, int R, double* Linv, const double* tol, unsigned long long* nclamp, cudaStream_t s);
+// Z [dim][R] <- Z V^-1 with V = L L^T from cholesky_blocked (in place)
+void chol_solve_right(const double* L, const double* Linv, int R, double* Z, int dim, cudaStream_t s);
+// U = Ut / lam (column 2-norms); zero column keeps lam = 0
+void normalise_cols(const double* Ut, int dim, int R, double* U, double* lam, cudaStream_t s);
+// out[0] = sum_{x,r} M[x][r] * Ut[x][r] (Ut = U * lam),  out[1] = lam^T (Ga.Gb.Gi.Gj) lam
+void fit_terms(const double* M, const double* U, const double* lam, int dim, int R,
+               const double* Ga, const double* Gb, const double* Gi, const double* Gj,
+               double* partial, double* out, cudaStream_t s);
+// hist[0..3] = {fit, inner, norm2, eta}; fit from terms[0], terms[1], *normR2 (NaN if *normR2 <= 0)
+void finish_fit(const double* terms, const double* normR2, double* hist, cudaStream_t s);
+// eta from norm2_new, norm2_old and the cross term lam1^T (prod_m X_m) lam0
+void eta_terms(const double* X0, const double* X1, const double* X2, const double* X3,
+               const double* lam1, const double* lam0, int R, double* partial, double* out, cudaStream_t s);
+void finish_eta(const double* cross, const double* norm2_new, const double* norm2_old, double* hist, cudaStream_t s);
+// M_i[i][r] = sum_j P[r][i*o+j] Uj[j][r]  (which = 0);  M_j[j][r] = sum_i P[r][i*o+j] Ui[i][r] (which = 1)
+void occ_mttkrp(const double* P, int ldP, const double* U, int o, int R, int which, double* M, cudaStream_t s);
+// energy: out = sum_r lam_r sum_Q [2 A(i,a) A(j,b) - A(i,b) A(j,a)], A from Z_a/Z_b [X][o][R]
+void energy_reduce(const double* Za, const double* Zb, const double* Ui, const double* Uj,
+                   const double* lam, int X, int o, int R, double* partial, double* out, cudaStream_t s);
+// g[i][a][j][b] buffer is built with gemm64; this reduces R-block [ab][v][o][o] against it
+void exact_reduce(const double* Rblk, int a0, int na, int v, int o, const double* g,
+                  double* partial, double* acc, cudaStream_t s);
+void sum_partials(const double* partial, int n, double* out, int accumulate, cudaStream_t s);
+void fill_f64(double* p, size_t n, double val, cudaStream_t s);
+
+// ---- tensor-core path (ppl_tc.cu) ------------------------------------------
+// Operands of the tcgen05 GEMM are K-major: rows of K contiguous elements.
+// BF16X3 keeps two planes (hi, lo) of bf16; TF32 keeps one plane of fp32
+// (already rounded to tf32).  A "plane" below is the hi plane; lo = hi + plane_elems.
+struct TcMat {
+    void* ptr;              // hi plane (bf16) or fp32 plane
+    long long plane_elems;  // distance to the lo plane in elements (BF16X3)
+    int rows, cols;         // cols = K extent; rows = M or N extent
+    int batch;              // 3rd dimension
+    long long ld;           // row stride in elements (multiple of 8)
+    long long bstride;      // batch stride in elements (multiple of 8)
+};
+// Epilogue: element (m, n) of batch b goes to
+//   out + b*sb + (m / mdiv)*sm_hi + (m % mdiv)*sm_lo + (n / ndiv)*sn_hi + (n % ndiv)*sn_lo
+enum TcEpi { EPI_SPLIT = 0, EPI_F32 = 1, EPI_ATOMIC_F64 = 2, EPI_ATOMIC_F32 = 3 };
+struct TcOut {
+    int kind;               // TcEpi; EPI_SPLIT writes operand planes of the same precision
+    void* out; long long plane_elems;
+    long long sb, sm_hi, sm_lo, sn_hi, sn_lo;
+    int mdiv, ndiv;
+    float alpha;
+};
+struct TcGemm {
+    int prec;               // PPL_PREC_BF16X3 or PPL_PREC_TF32
+    TcMat A, B;             // A: [batch][M][K], B: [batch][N][K]
+    int M, N, K, batch;
+    int a_row0, b_row0;     // row offsets into A and B
+    int a_b0, b_b0;         // batch offsets; a_bstep / b_bstep: 0 broadcasts one batch entry
+    int a_bstep, b_bstep;
+    int ksplit;             // split-K factor (atomic epilogues only)
+    int bn;                 // N tile (multiple of 16, <= 256); 0 = automatic
+    TcOut out;
+};
+int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);
+int tc_init_driver();   // resolves cuTensorMapEncodeTiled; returns 0 on success
+// FP64 -> operand planes: dst[b][r][c] from src with generic index maps, rows x cols per batch
+struct SplitSrc {
+    const double* src; Idx2 rmap, cmap; long long bstride;
+    const float* src32;    // alternative FP32 source (for ppl_tc_gemm)
+};
+void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch,
+                      void* dst, long long plane_elems, long long ld, long long bstride, cudaStream_t st);
+void zero_bytes(void* p, size_t n, cudaStream_t s);

@@ -1,0 +1,476 @@
+// Tensor-core contraction for the MTTKRP steps of the CP-ALS sweep on sm_103a.
+//
+// C[b][m][n] = sum_k A[b][m][k] B[b][n][k], both operands K-major in global
+// memory, staged by TMA (128-byte swizzle, no multicast) into a ring of
+// shared-memory stages and multiplied by tcgen05.mma with the FP32
+// accumulator in tensor memory.  Two operand precisions:
+//   BF16X3: x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the product is
+//           hi*hi + hi*lo + lo*hi (three MMAs into one accumulator), after
+//           Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial
+//           intelligence datatype for higher-precision computations" (2019);
+//   TF32:   operands rounded to tf32 (round to nearest) when written, one MMA.
+// One CTA of 128 threads computes one 128 x bn tile: lane 0 of warp 0 issues
+// TMA, lane 0 of warp 1 issues MMAs, warp 2 owns the TMEM allocation, and all
+// four warps run the epilogue (warp w reads TMEM lanes 32w..32w+31).
+// Every mbarrier wait is bounded; on expiry the kernel records the error,
+// drains what it issued, frees TMEM and returns.
+#include "ppl_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/ppl_cpd.h"
+
+namespace {
+
+constexpr int TM = 128;               // rows of the accumulator tile (TMEM lanes)
+constexpr int KROW_BYTES = 128;       // one swizzle row: 64 bf16 or 32 fp32
+constexpr int SMEM_BUDGET = 200 * 1024;
+constexpr unsigned long long WAIT_NS = 500ull * 1000ull * 1000ull;   // 0.5 s per wait
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+struct KParams {
+    int M, N, K, bn, ksplit, nkb_total, per_split, stages;
+    int a_row0, b_row0, a_b0, b_b0, a_bstep, b_bstep;
+    int batch;
+    int kind;
+    void* out;
+    long long plane, sb, sm_hi, sm_lo, sn_hi, sn_lo;
+    int mdiv, ndiv;
+    float alpha;
+    unsigned int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: true when the phase completed, false after WAIT_NS
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        if (mbar_try(a, parity)) return true;
+        if (gtimer() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ unsigned long long make_desc(uint32_t saddr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= 1ull << 16;                       // leading byte offset (unused for swizzled K-major)
+    d |= (unsigned long long)(1024 >> 4) << 32;   // stride byte offset
+    d |= 1ull << 46;                       // descriptor version
+    d |= 2ull << 61;                       // SWIZZLE_128B
+    return d;
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t tmem, unsigned long long ad, unsigned long long bd, uint32_t idesc,
+                                    uint32_t acc) {
+    if constexpr (PREC == PPL_PREC_BF16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
+    constexpr bool SPLIT = (PREC == PPL_PREC_BF16X3);
+    constexpr int KE = SPLIT ? 64 : 32;       // elements per 128-byte row
+    constexpr int KSTEP = SPLIT ? 16 : 8;     // K per MMA instruction
+    constexpr int ASTEP_BYTES = KSTEP * (SPLIT ? 2 : 4);   // 32 bytes
+
+    const int bz = blockIdx.z / p.ksplit, ks = blockIdx.z % p.ksplit;
+    const int kb0 = ks * p.per_split;
+    int nk = p.nkb_total - kb0;
+    if (nk > p.per_split) nk = p.per_split;
+    if (nk <= 0) return;   // empty split-K slice: nothing to add
+
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * p.bn;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+
+    const uint32_t a_bytes = TM * KROW_BYTES;
+    const uint32_t b_bytes = (uint32_t)p.bn * KROW_BYTES;
+    const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (a_bytes + b_bytes);
+    const uint32_t bar_off = stage_bytes * p.stages;
+    const uint32_t full0 = base + bar_off;                 // stages x 8 bytes
+    const uint32_t empty0 = full0 + 8u * p.stages;
+    const uint32_t done_bar = empty0 + 8u * p.stages;
+    const uint32_t slot = done_bar + 8u;                   // TMEM address slot
+    volatile uint32_t* slot_ptr = (volatile uint32_t*)(gbase + bar_off + 16u * p.stages + 8u);
+    __shared__ int s_fail;
+
+    uint32_t ncols = 32;
+    while ((int)ncols < p.bn) ncols <<= 1;
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < p.stages; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, 1);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mAh) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mBh) : "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot_ptr;
+
+    int issued = 0, consumed = 0;
+    const int a_b = p.a_b0 + bz * p.a_bstep;
+    const int b_b = p.b_b0 + bz * p.b_bstep;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int it = 0; it < nk; ++it) {
+            const int s = it % p.stages;
+            if (it >= p.stages) {
+                if (!mbar_wait(empty0 + 8u * s, (uint32_t)((it / p.stages - 1) & 1))) {
+                    atomicOr(p.err, 1u);
+                    s_fail = 1;
+                    break;
+                }
+            }
+            if (*(volatile int*)&s_fail) break;
+            const uint32_t sa = base + stage_bytes * s;
+            const uint32_t fb = full0 + 8u * s;
+            mbar_expect_tx(fb, stage_bytes);
+            const int kc = (kb0 + it) * KE;
+            tma_load_3d(sa, &mAh, kc, p.a_row0 + m0, a_b, fb);
+            tma_load_3d(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, kc, p.b_row0 + n0, b_b, fb);
+            if constexpr (SPLIT) {
+                tma_load_3d(sa + a_bytes, &mAl, kc, p.a_row0 + m0, a_b, fb);
+                tma_load_3d(sa + 2u * a_bytes + b_bytes, &mBl, kc, p.b_row0 + n0, b_b, fb);
+            }
+            issued = it + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
+        idesc |= SPLIT ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+        for (int it = 0; it < nk; ++it) {
+            const int s = it % p.stages;
+            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / p.stages) & 1))) {
+                atomicOr(p.err, 2u);
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + stage_bytes * s;
+            const uint32_t sah = sa, sal = sa + a_bytes;
+            const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+            const int kc = (kb0 + it) * KE;
+            int ksteps = KE / KSTEP;
+            if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+            const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+            const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+            for (int kk = 0; kk < ksteps; ++kk) {
+                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                mma<PREC>(tmem, dah + off, dbh + off, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                if constexpr (SPLIT) {
+                    mma<PREC>(tmem, dah + off, dbl + off, idesc, 1u);
+                    mma<PREC>(tmem, dal + off, dbh + off, idesc, 1u);
+                }
+            }
+            mma_commit(empty0 + 8u * s);
+            consumed = it + 1;
+        }
+        mma_commit(done_bar);
+    }
+    __syncwarp();
+
+    // epilogue: wait for the accumulator
+    bool ok = mbar_wait(done_bar, 0);
+    if (!ok) {
+        if (lane == 0) atomicOr(p.err, 4u);
+        s_fail = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool failed = (*(volatile int*)&s_fail) != 0;
+
+    if (!failed) {
+        const int m = m0 + warp * 32 + lane;
+        const bool mrow = (m < p.M);
+        long long mo = 0;
+        if (mrow) mo = (long long)bz * p.sb + (long long)(m / p.mdiv) * p.sm_hi + (long long)(m % p.mdiv) * p.sm_lo;
+        for (int c0 = 0; c0 < p.bn; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (!mrow) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c0 + j;
+                if (n >= p.N) break;
+                const long long idx = mo + (long long)(n / p.ndiv) * p.sn_hi + (long long)(n % p.ndiv) * p.sn_lo;
+                const float x = p.alpha * __uint_as_float(v[j]);
+                if (p.kind == EPI_SPLIT) {
+                    if constexpr (SPLIT) {
+                        __nv_bfloat16* o = (__nv_bfloat16*)p.out;
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                        o[idx] = hi;
+                        o[idx + p.plane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                    } else {
+                        ((float*)p.out)[idx] = round_tf32(x);
+                    }
+                } else if (p.kind == EPI_F32) {
+                    ((float*)p.out)[idx] = x;
+                } else if (p.kind == EPI_ATOMIC_F64) {
+                    atomicAdd((double*)p.out + idx, (double)x);
+                } else {
+                    atomicAdd((float*)p.out + idx, x);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        // drain TMA writes that were issued but never consumed
+        for (int it = consumed; it < issued; ++it) {
+            const int s = it % p.stages;
+            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / p.stages) & 1))) break;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// ---- operand preparation -----------------------------------------------------
+
+__device__ __forceinline__ long long ixd(const Idx2& x, int i) {
+    return (long long)(i / x.div) * x.hi + (long long)(i % x.div) * x.lo;
+}
+
+template <int PREC>
+__global__ void k_split(SplitSrc s, int rows, int cols, int batch, void* dst, long long plane, long long ld,
+                        long long bstride) {
+    const long long per = (long long)rows * ld;
+    const long long total = per * batch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / per);
+        const long long rc = e % per;
+        const int r = (int)(rc / ld), c = (int)(rc % ld);
+        float x = 0.0f;
+        double xd = 0.0;
+        if (c < cols) {
+            if (s.src32)
+                xd = (double)s.src32[(long long)b * s.bstride + ixd(s.rmap, r) + ixd(s.cmap, c)];
+            else
+                xd = s.src[(long long)b * s.bstride + ixd(s.rmap, r) + ixd(s.cmap, c)];
+        }
+        const long long di = (long long)b * bstride + (long long)r * ld + c;
+        if constexpr (PREC == PPL_PREC_BF16X3) {
+            const __nv_bfloat16 hi = __double2bfloat16(xd);
+            const __nv_bfloat16 lo = __double2bfloat16(xd - (double)__bfloat162float(hi));
+            ((__nv_bfloat16*)dst)[di] = hi;
+            ((__nv_bfloat16*)dst)[di + plane] = lo;
+        } else {
+            x = (float)xd;
+            ((float*)dst)[di] = round_tf32(x);
+        }
+    }
+}
+
+bool make_map(CUtensorMap* m, int prec, const void* ptr, const TcMat& t, int box_rows) {
+    const bool split = (prec == PPL_PREC_BF16X3);
+    const size_t es = split ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows, (cuuint64_t)(t.batch > 0 ? t.batch : 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)(t.ld * es), (cuuint64_t)((t.bstride > 0 ? t.bstride : t.ld * t.rows) * es)};
+    cuuint32_t box[3] = {(cuuint32_t)(KROW_BYTES / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(m, split ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int choose_bn(int N) {
+    int tiles = (N + 255) / 256;
+    int bn = (N + tiles - 1) / tiles;
+    bn = (bn + 15) / 16 * 16;
+    if (bn < 16) bn = 16;
+    if (bn > 256) bn = 256;
+    return bn;
+}
+
+inline int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+int tc_init_driver() {
+    if (g_encode) return 0;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return -1;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_done = true;
+    }
+    return 0;
+}
+
+int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0 || g.K <= 0) return 0;
+    if (tc_init_driver() != 0) return -1;
+    const bool split = (g.prec == PPL_PREC_BF16X3);
+    const int KE = split ? 64 : 32;
+    KParams p{};
+    p.M = g.M; p.N = g.N; p.K = g.K;
+    p.bn = g.bn > 0 ? g.bn : choose_bn(g.N);
+    p.nkb_total = (g.K + KE - 1) / KE;
+    p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
+    if (p.ksplit > p.nkb_total) p.ksplit = p.nkb_total;
+    p.per_split = (p.nkb_total + p.ksplit - 1) / p.ksplit;
+    p.ksplit = (p.nkb_total + p.per_split - 1) / p.per_split;
+    const int stage_bytes = (split ? 2 : 1) * (TM + p.bn) * KROW_BYTES;
+    p.stages = SMEM_BUDGET / stage_bytes;
+    if (p.stages > 8) p.stages = 8;
+    if (p.stages < 2) return -2;
+    p.a_row0 = g.a_row0; p.b_row0 = g.b_row0; p.a_b0 = g.a_b0; p.b_b0 = g.b_b0;
+    p.a_bstep = g.a_bstep; p.b_bstep = g.b_bstep;
+    p.batch = g.batch;
+    p.kind = g.out.kind; p.out = g.out.out; p.plane = g.out.plane_elems;
+    p.sb = g.out.sb; p.sm_hi = g.out.sm_hi; p.sm_lo = g.out.sm_lo; p.sn_hi = g.out.sn_hi; p.sn_lo = g.out.sn_lo;
+    p.mdiv = g.out.mdiv > 0 ? g.out.mdiv : (1 << 30);
+    p.ndiv = g.out.ndiv > 0 ? g.out.ndiv : (1 << 30);
+    p.alpha = g.out.alpha;
+    p.err = err_flag;
+
+    CUtensorMap mAh, mAl, mBh, mBl;
+    const size_t es = split ? 2 : 4;
+    if (!make_map(&mAh, g.prec, g.A.ptr, g.A, TM) || !make_map(&mBh, g.prec, g.B.ptr, g.B, p.bn)) return -3;
+    if (split) {
+        if (!make_map(&mAl, g.prec, (const char*)g.A.ptr + g.A.plane_elems * es, g.A, TM) ||
+            !make_map(&mBl, g.prec, (const char*)g.B.ptr + g.B.plane_elems * es, g.B, p.bn))
+            return -3;
+    } else {
+        mAl = mAh;
+        mBl = mBh;
+    }
+    const size_t smem = (size_t)stage_bytes * p.stages + 1024 + 16 * p.stages + 64;
+    dim3 grid((g.M + TM - 1) / TM, (g.N + p.bn - 1) / p.bn, g.batch * p.ksplit);
+    if (grid.y > 65535 || grid.z > 65535) return -4;
+    if (split)
+        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    else
+        k_tc_gemm<PPL_PREC_TF32><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    return cudaGetLastError() == cudaSuccess ? 0 : -5;
+}
+
+void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch, void* dst, long long plane_elems,
+                      long long ld, long long bstride, cudaStream_t st) {
+    const long long total = (long long)rows * ld * batch;
+    if (total <= 0) return;
+    if (prec == PPL_PREC_BF16X3)
+        k_split<PPL_PREC_BF16X3><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,
+                                                                       bstride);
+    else
+        k_split<PPL_PREC_TF32><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,
+                                                                     bstride);
+}
+
+void zero_bytes(void* p, size_t n, cudaStream_t s) {
+    if (n) cudaMemsetAsync(p, 0, n, s);
+}

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/ppl_cpd.h declares, and rejects bad arguments
+before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2503_10380_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    try:
+        __graft_entry__.build()
+    except RuntimeError as e:   # no nvcc on this machine
+        pytest.skip(str(e))
+    return binding.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ppl_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_workspace_size_validates(lib):
+    o = binding.make_opts("bf16x3")
+    with pytest.raises(binding.PplError) as e:
+        binding.ppl_cpd_workspace_size(0, 24, 72, 48, o)
+    assert e.value.code == binding.PPL_EINVAL
+    o.precision = 9
+    with pytest.raises(binding.PplError):
+        binding.ppl_cpd_workspace_size(5, 24, 72, 48, o)
+
+
+def test_workspace_grows_with_rank_and_precision_layout(lib):
+    f64 = binding.ppl_cpd_workspace_size(5, 24, 72, 48, binding.make_opts("fp64"))
+    b16 = binding.ppl_cpd_workspace_size(5, 24, 72, 48, binding.make_opts("bf16x3"))
+    t32 = binding.ppl_cpd_workspace_size(5, 24, 72, 48, binding.make_opts("tf32"))
+    big = binding.ppl_cpd_workspace_size(5, 24, 72, 96, binding.make_opts("bf16x3"))
+    assert b16 == t32 and big > b16 and f64 > 0
+
+
+def test_init_rejects_small_workspace_and_null(lib):
+    opts = binding.make_opts("fp64")
+    need = binding.ppl_cpd_workspace_size(5, 24, 72, 48, opts)
+    h = ctypes.c_void_p()
+    fake = 1 << 20   # never dereferenced: the checks run before any CUDA call
+    rc = lib.ppl_cpd_init(ctypes.byref(h), 5, 24, 72, 48, fake, fake, fake, fake, need - 1,
+                          ctypes.byref(opts), None)
+    assert rc == binding.PPL_ENOMEM
+    assert b"needs" in lib.ppl_last_error(None)
+    rc = lib.ppl_cpd_init(ctypes.byref(h), 5, 24, 72, 48, None, fake, fake, fake, need, ctypes.byref(opts), None)
+    assert rc == binding.PPL_EINVAL
+    rc = lib.ppl_cpd_init(ctypes.byref(h), 5, 24, 72, 48, fake, fake, fake, fake + 8, need, ctypes.byref(opts), None)
+    assert rc == binding.PPL_EINVAL   # misaligned workspace
+    assert lib.ppl_cpd_destroy(None) == binding.PPL_OK
+
+
+def test_handle_calls_reject_null_handle(lib):
+    x = ctypes.c_double()
+    assert lib.ppl_cpd_fit(None, ctypes.byref(x)) == binding.PPL_EINVAL
+    assert lib.ppl_cpd_sweep(None, 1, None) == binding.PPL_EINVAL
+    assert lib.ppl_cpd_mttkrp(None, 0, None) == binding.PPL_EINVAL

@@ -1,0 +1,173 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Sizes span several tiles and ragged tails.  Tolerances:
+* FP64 form: 1e-12 relative for one MTTKRP (a few hundred FP64 roundings of
+  O(1) terms), 1e-8 after several ALS sweeps (Cholesky solves amplify
+  rounding by the condition number of V).
+* BF16X3: each operand is split into bf16 hi + lo with |x - hi - lo| <= 2^-16 |x|;
+  dropping lo*lo leaves <= 3 * 2^-16 relative per product, FP32 accumulation
+  adds K * 2^-24.  The MTTKRP chains four contractions, so the normwise
+  bound is about 4 * (3 * 2^-16) ~ 2e-4; the tests use 1e-4 normwise
+  (errors add in quadrature in practice).
+* TF32: operands rounded to nearest with 10 explicit bits, |dx| <= 2^-11 |x|,
+  i.e. about 2 * 2^-11 = 1e-3 per product and 4e-3 for the chain; tests use 4e-3.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ppl_oracle as orc
+from paper_2503_10380_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_MTTKRP = {"fp64": 1e-12, "bf16x3": 1e-4, "tf32": 4e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+SHAPES = [
+    (5, 24, 72, 48),     # config 0
+    (3, 13, 17, 19),     # every extent ragged
+    (1, 9, 5, 1),        # o = 1, R = 1
+    (7, 40, 90, 150),    # several tiles, ragged tails
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 600, 200), (37, 130, 1000), (300, 16, 24)])
+def test_tc_gemm_building_block(prec, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    C = binding.tc_gemm(_dev(A), _dev(B), prec).cpu().numpy()
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    bound = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T
+    tol = 3 * 2.0 ** -16 + K * 2.0 ** -24 if prec == "bf16x3" else 2 * 2.0 ** -11 + K * 2.0 ** -24
+    assert np.all(np.abs(C - ref) <= tol * bound + 1e-30)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_mttkrp_each_mode(prec, shape):
+    o, v, X, R = shape
+    inp = inputs.make_inputs(o, v, X, R, seed=1)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec)
+    for m in orc.MODES:
+        M = cp.mttkrp(m).cpu().numpy()
+        ref = orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m)
+        assert _rel(M, ref) < TOL_MTTKRP[prec], (m, _rel(M, ref))
+    cp.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp64_sweeps_match_oracle(shape):
+    o, v, X, R = shape
+    inp = inputs.make_inputs(o, v, X, R, seed=2)
+    n2, _ = orc.exact_contract(inp.B, inp.tau, o)
+    U_ref, lam_ref, hist = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 4, n2)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="fp64", want_eta=True)
+    cp.set_normR2(n2)
+    fits = cp.sweep(4)
+    f = {k: t.cpu().numpy() for k, t in cp.factors().items()}
+    for m in orc.MODES:
+        assert _rel(f[m], U_ref[m]) < 1e-8, m
+    assert _rel(f["lam"], lam_ref) < 1e-8
+    for k in range(4):
+        assert abs(fits[k] - hist[k]["fit"]) < 1e-9
+    st = cp.stats()
+    assert abs(st["last_eta"] - hist[-1]["eta"]) < 1e-8 * max(hist[-1]["eta"], 1e-3)
+    assert st["clamped_pivots"] == sum(h["nclamped"] for h in hist)
+    cp.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3])
+def test_exact_contraction_and_energies(shape):
+    o, v, X, R = shape
+    inp = inputs.make_inputs(o, v, X, R, seed=3)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="fp64")
+    n2, E, Rt = cp.exact_contract(want_R=True)
+    R_ref = orc.ppl_tensor(inp.Bvv, inp.tau)
+    assert _rel(Rt.cpu().numpy(), R_ref) < 1e-13
+    assert abs(n2 - float(np.sum(R_ref ** 2))) < 1e-12 * n2
+    assert abs(E - orc.energy_of_tensor(R_ref, inp.B, o)) < 1e-12 * abs(E)
+    lam1 = np.ones(R)
+    E_cp = cp.energy()
+    assert abs(E_cp - orc.energy_cp(inp.B, o, inp.factors, lam1)) < 1e-12 * abs(E_cp)
+    cp.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_mixed_sweeps_track_fp64_energy(prec):
+    """Config 0: 20 sweeps in mixed precision from the same start as the FP64
+    oracle; the CP energy agrees within 0.1 kcal/mol."""
+    inp = inputs.make_inputs(5, 24, 72, 48, seed=0)
+    n2, _ = orc.exact_contract(inp.B, inp.tau, 5)
+    U_ref, lam_ref, hist = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 20, n2)
+    E_ref = orc.energy_cp(inp.B, 5, U_ref, lam_ref)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec)
+    cp.set_normR2(n2)
+    fits = cp.sweep(20)
+    E = cp.energy()
+    kcal = 627.509474
+    assert abs(E - E_ref) * kcal < 0.1
+    assert abs(fits[-1] - hist[-1]["fit"]) < 1e-3
+    cp.close()
+
+
+def test_graph_replay_equals_direct_launches():
+    inp = inputs.make_inputs(4, 20, 30, 40, seed=5)
+    out = []
+    for use_graph in (False, True):
+        cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3", use_graph=use_graph)
+        cp.sweep(3)
+        out.append({k: t.cpu().numpy().copy() for k, t in cp.factors().items()})
+        cp.close()
+    for k in out[0]:
+        assert _rel(out[1][k], out[0][k]) < 1e-6
+
+
+def test_warm_start_set_tau():
+    inp = inputs.make_inputs(4, 16, 24, 20, seed=6)
+    tau1 = inp.tau + inputs.tau_increment(inp.tau, 1, seed=6)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="fp64")
+    cp.sweep(3)
+    U0 = {k: t.cpu().numpy().copy() for k, t in cp.factors().items()}
+    t1 = _dev(tau1)
+    cp.set_tau(t1)
+    cp.sweep(2)
+    U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, tau1, {m: U0[m] for m in orc.MODES}, 2, lam0=U0["lam"])
+    f = {k: t.cpu().numpy() for k, t in cp.factors().items()}
+    for m in orc.MODES:
+        assert _rel(f[m], U_ref[m]) < 1e-9
+    cp.close()
+
+
+def test_errors_are_reported_not_raised_in_c():
+    inp = inputs.make_inputs(2, 8, 10, 6, seed=7)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="fp64")
+    with pytest.raises(binding.PplError) as e:
+        cp.fit()
+    assert e.value.code == binding.PPL_ENOTREADY
+    with pytest.raises(binding.PplError) as e:
+        binding.ppl_cpd_mttkrp(cp.h, 7, 0)
+    assert e.value.code == binding.PPL_EINVAL
+    cp.close()
