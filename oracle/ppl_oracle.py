@@ -112,16 +112,22 @@ def dbar_r(Bvv: np.ndarray, U: np.ndarray) -> np.ndarray:
     return np.tensordot(U, Bvv, axes=([0], [1]))      # [r, Q, d]
 
 
+def compound_view(Bvv):
+    """D^{aQ}_c as a v x (X v) matrix over the compound index {Q c} (Eq. foreachr)."""
+    X, v, _ = Bvv.shape
+    return np.ascontiguousarray(Bvv.transpose(1, 0, 2)).reshape(v, X * v)
+
+
 def mttkrp_a(Bvv, T, Db):
     """Mode a (alpha), Eqs. (distribute) and (foreachr): for each r, the gemm
-    inner[Q, c] = sum_d Db[r, Q, d] T[r, c, d], then the contraction over the
+    inner[Q, c] = sum_d Db[r, Q, d] T[r, c, d], then the gemv over the
     compound index {Q c} with D^{aQ}_c."""
-    v = Bvv.shape[1]
+    Bc = compound_view(Bvv)
     R = T.shape[0]
-    M = np.zeros((v, R))
+    M = np.zeros((Bc.shape[0], R))
     for r in range(R):
         inner = Db[r] @ T[r].T                           # [Q, c]
-        M[:, r] = np.tensordot(Bvv, inner, axes=([0, 2], [0, 1]))
+        M[:, r] = Bc @ inner.reshape(-1)
     return M
 
 
@@ -129,12 +135,12 @@ def mttkrp_b(Bvv, T, Da):
     """Mode b (beta), the same chain with the roles of (a, c) and (b, d)
     exchanged: inner[Q, d] = sum_c Da[r, Q, c] T[r, c, d], then
     M[b, r] = sum_{Q d} B[Q, b, d] inner[Q, d]."""
-    v = Bvv.shape[1]
+    Bc = compound_view(Bvv)
     R = T.shape[0]
-    M = np.zeros((v, R))
+    M = np.zeros((Bc.shape[0], R))
     for r in range(R):
         inner = Da[r] @ T[r]                             # [Q, d]
-        M[:, r] = np.tensordot(Bvv, inner, axes=([0, 2], [0, 1]))
+        M[:, r] = Bc @ inner.reshape(-1)
     return M
 
 
