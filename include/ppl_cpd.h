@@ -62,7 +62,8 @@ typedef struct {
     int r_chunk;     /* columns of r processed per pass of the fused chain; 0 = automatic */
     int use_graph;   /* 1: capture one sweep in a CUDA graph on first use and replay it  */
     int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
-    int reserved[12];
+    int profile;     /* 1: record CUDA events between the phases of every sweep           */
+    int reserved[11];
 } ppl_cpd_opts;
 
 typedef struct {
@@ -74,6 +75,7 @@ typedef struct {
     double    last_inner;      /* <R, R~> after the last sweep                            */
     double    last_norm2;      /* ||R~||^2 after the last sweep, Eq. (cp_norm2)           */
     double    flops_per_sweep; /* algorithmic MTTKRP flops per sweep, 4 o^2 v^2 R + 16 X v^2 R */
+    long long kernels_per_sweep; /* kernel nodes in the captured sweep graph (0 before capture) */
 } ppl_cpd_stats;
 
 /* Fill *opts with defaults: BF16X3, automatic r_chunk, graphs on, eta off. */
@@ -134,6 +136,13 @@ int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_ou
  * (the paper's "Optimal guess", Role of the Initial Guess section).  The
  * stored ||R||^2 is forgotten. */
 int ppl_cpd_set_tau(ppl_cpd* h, const double* tau);
+
+/* Device time of the phases of the last sweep, in ms (needs opts.profile = 1):
+ *   ms[0] tau^{cd}_r (Khatri-Rao build + T contraction)   ms[1] MTTKRP chain, mode a
+ *   ms[2] solve a    ms[3] MTTKRP chain, mode b    ms[4] solve b
+ *   ms[5] S and P contractions (modes i, j)    ms[6] solves i and j    ms[7] fit terms
+ * ENOTREADY if profiling is off or no sweep has run. */
+int ppl_cpd_phase_ms(ppl_cpd* h, double* ms);
 
 /* Counters and the last sweep's scalars. */
 int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* stats);

@@ -23,13 +23,14 @@ STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4
 
 class ppl_cpd_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
-                ("reserved", c_int * 12)]
+                ("profile", c_int), ("reserved", c_int * 11)]
 
 
 class ppl_cpd_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_longlong), ("clamped_pivots", ctypes.c_longlong),
                 ("timeouts", ctypes.c_longlong), ("last_fit", c_double), ("last_eta", c_double),
-                ("last_inner", c_double), ("last_norm2", c_double), ("flops_per_sweep", c_double)]
+                ("last_inner", c_double), ("last_norm2", c_double), ("flops_per_sweep", c_double),
+                ("kernels_per_sweep", ctypes.c_longlong)]
 
 
 class PplError(RuntimeError):
@@ -63,6 +64,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_exact_contract.argtypes = [H, POINTER(c_double), POINTER(c_double), c_void_p]
     L.ppl_cpd_set_tau.argtypes = [H, c_void_p]
     L.ppl_cpd_stats_get.argtypes = [H, POINTER(ppl_cpd_stats)]
+    L.ppl_cpd_phase_ms.argtypes = [H, POINTER(c_double)]
     L.ppl_last_error.argtypes = [H]
     L.ppl_last_error.restype = c_char_p
     L.ppl_cpd_destroy.argtypes = [H]
@@ -71,7 +73,7 @@ def lib() -> ctypes.CDLL:
                               c_void_p]
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
-                 "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy",
+                 "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -84,13 +86,14 @@ def _check(rc: int, h=None):
         raise PplError(rc, msg.decode() if msg else "")
 
 
-def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False) -> ppl_cpd_opts:
+def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, profile=False) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.r_chunk = int(r_chunk)
     o.use_graph = int(bool(use_graph))
     o.want_eta = int(bool(want_eta))
+    o.profile = int(bool(profile))
     return o
 
 
@@ -151,6 +154,15 @@ def ppl_cpd_stats_get(h) -> dict:
     return {k: getattr(s, k) for k, _ in ppl_cpd_stats._fields_}
 
 
+PHASES = ("tau_r", "chain_a", "solve_a", "chain_b", "solve_b", "s_and_p", "solve_ij", "fit")
+
+
+def ppl_cpd_phase_ms(h) -> dict:
+    buf = (c_double * 8)()
+    _check(lib().ppl_cpd_phase_ms(h, buf), h)
+    return dict(zip(PHASES, list(buf)))
+
+
 def ppl_cpd_destroy(h):
     _check(lib().ppl_cpd_destroy(h))
 
@@ -177,7 +189,7 @@ class CpAls:
     """
 
     def __init__(self, B, tau, factors, precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False,
-                 stream=None):
+                 profile=False, stream=None):
         import torch
         self.torch = torch
         X, n, _ = B.shape
@@ -192,7 +204,7 @@ class CpAls:
         parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
         parts.append(torch.ones(R, dtype=torch.float64))
         self.fac = torch.cat(parts).to(dev)
-        self.opts = make_opts(precision, r_chunk, use_graph, want_eta)
+        self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile)
         self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -240,6 +252,9 @@ class CpAls:
 
     def stats(self) -> dict:
         return ppl_cpd_stats_get(self.h)
+
+    def phase_ms(self) -> dict:
+        return ppl_cpd_phase_ms(self.h)
 
     def close(self):
         if self.h:

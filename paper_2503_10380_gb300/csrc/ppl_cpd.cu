@@ -145,6 +145,9 @@ struct ppl_cpd {
     bool graph_ready;
     double last_hist[4];
     std::string err;
+    cudaEvent_t pev[9];
+    bool have_pev;
+    long long kernels_per_sweep;
 
     template <class T>
     T* at(size_t off) const { return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(ws + off); }
@@ -228,7 +231,9 @@ int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
     g.prec = h->opts.precision;
     if (g.bn == 0) g.bn = bn_for(g.N);
     const int r = tc_gemm(g, h->errflag(), h->st);
-    if (r != 0) return fail(h, PPL_ECUDA, "tensor-core GEMM (%s) failed to launch (%d)", what, r);
+    if (r != 0)
+        return fail(h, PPL_ECUDA, "tensor-core GEMM (%s) failed to launch (%d%s%s)", what, r, r <= -1000 ? ": " : "",
+                    r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
     return PPL_OK;
 }
 
@@ -534,6 +539,10 @@ void cross_gram(ppl_cpd* h, int m) {
     gemm64(g, h->st);
 }
 
+void mark(ppl_cpd* h, int k) {
+    if (h->opts.profile) cudaEventRecord(h->pev[k], h->st);
+}
+
 int sweep_body(ppl_cpd* h) {
     const int o = h->o, v = h->v, R = h->R;
     double* M = h->at<double>(h->L.M);
@@ -546,26 +555,39 @@ int sweep_body(ppl_cpd* h) {
                         h->st);
     }
     int e;
+    mark(h, 0);
     if (h->tc()) {
         if ((e = t_tc(h))) return e;
+        mark(h, 1);
         if ((e = chain_tc(h, 0, M))) return e;
+        mark(h, 2);
         solve_mode(h, 0);
+        mark(h, 3);
         if ((e = chain_tc(h, 1, M))) return e;
+        mark(h, 4);
         solve_mode(h, 1);
+        mark(h, 5);
         if ((e = p_tc(h))) return e;
     } else {
         t_fp64(h);
+        mark(h, 1);
         mttkrp_ab_fp64(h, 0, M);
+        mark(h, 2);
         solve_mode(h, 0);
+        mark(h, 3);
         mttkrp_ab_fp64(h, 1, M);
+        mark(h, 4);
         solve_mode(h, 1);
+        mark(h, 5);
         p_fp64(h);
     }
+    mark(h, 6);
     double* P = h->at<double>(h->L.P);
     occ_mttkrp(P, R, h->U[3], o, R, 0, M, h->st);
     solve_mode(h, 2);
     occ_mttkrp(P, R, h->U[2], o, R, 1, M, h->st);
     solve_mode(h, 3);
+    mark(h, 7);
     double* sc = h->scal();
     fit_terms(M, h->U[3], h->lam, o, R, h->G(0), h->G(1), h->G(2), h->G(3), h->at<double>(h->L.partial),
               sc + SC_TERMS, h->st);
@@ -578,6 +600,7 @@ int sweep_body(ppl_cpd* h) {
         finish_eta(sc + SC_CROSS, sc + SC_TERMS + 1, sc + SC_NORM2_PREV, hist, h->st);
         cudaMemcpyAsync(sc + SC_NORM2_PREV, sc + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st);
     }
+    mark(h, 8);
     (void)v;
     return check_cuda(h, "sweep");
 }
@@ -667,6 +690,17 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     h->normR2 = 0.0; h->have_normR2 = false; h->sweeps = 0;
     h->graph = nullptr; h->gexec = nullptr; h->graph_ready = false;
     for (double& x : h->last_hist) x = nan("");
+    h->have_pev = false;
+    h->kernels_per_sweep = 0;
+    if (op.profile) {
+        for (int k = 0; k < 9; ++k)
+            if (cudaEventCreate(&h->pev[k]) != cudaSuccess) {
+                cudaGetLastError();
+                delete h;
+                return fail(nullptr, PPL_ECUDA, "could not create profiling events");
+            }
+        h->have_pev = true;
+    }
     if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -741,6 +775,20 @@ int ppl_cpd_sweep(ppl_cpd* h, int nsweeps, double* fit_hist) {
                 }
                 h->graph = gr;
                 h->graph_ready = true;
+                size_t nn = 0;
+                cudaGraphGetNodes(gr, nullptr, &nn);
+                if (nn) {
+                    cudaGraphNode_t* nodes = new cudaGraphNode_t[nn];
+                    cudaGraphGetNodes(gr, nodes, &nn);
+                    long long kc = 0;
+                    for (size_t q = 0; q < nn; ++q) {
+                        cudaGraphNodeType t;
+                        cudaGraphNodeGetType(nodes[q], &t);
+                        if (t == cudaGraphNodeTypeKernel) ++kc;
+                    }
+                    delete[] nodes;
+                    h->kernels_per_sweep = kc;
+                }
             }
             cudaGraphLaunch(h->gexec, h->st);
         } else {
@@ -857,6 +905,7 @@ int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_ou
 
 int ppl_cpd_set_tau(ppl_cpd* h, const double* tau) {
     if (!h || !tau) return fail(h, PPL_EINVAL, "NULL argument");
+    const bool same = (tau == h->tau);
     h->tau = tau;
     h->have_normR2 = false;
     h->normR2 = 0.0;
@@ -868,7 +917,7 @@ int ppl_cpd_set_tau(ppl_cpd* h, const double* tau) {
     if (!e) e = sync_and_check(h);
     leave(h);
     // the FP64 form reads tau through its pointer, which a captured graph has baked in
-    if (h->graph_ready) {
+    if (h->graph_ready && !same) {
         cudaGraphExecDestroy(h->gexec);
         cudaGraphDestroy(h->graph);
         h->gexec = nullptr;
@@ -892,6 +941,7 @@ int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
     s->last_eta = h->opts.want_eta ? h->last_hist[3] : nan("");
     const double o = h->o, v = h->v, X = h->X, R = h->R;
     s->flops_per_sweep = 4.0 * o * o * v * v * R + 16.0 * X * v * v * R;
+    s->kernels_per_sweep = h->kernels_per_sweep;
     return check_cuda(h, "stats");
 }
 
@@ -905,7 +955,24 @@ int ppl_cpd_destroy(ppl_cpd* h) {
     cudaStreamDestroy(h->st);
     cudaEventDestroy(h->ev_in);
     cudaEventDestroy(h->ev_out);
+    if (h->have_pev)
+        for (int k = 0; k < 9; ++k) cudaEventDestroy(h->pev[k]);
     delete h;
+    return PPL_OK;
+}
+
+int ppl_cpd_phase_ms(ppl_cpd* h, double* ms) {
+    if (!h || !ms) return fail(h, PPL_EINVAL, "NULL argument");
+    if (!h->have_pev || h->sweeps == 0) return fail(h, PPL_ENOTREADY, "profiling off or no sweep has run");
+    cudaStreamSynchronize(h->st);
+    for (int k = 0; k < 8; ++k) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, h->pev[k], h->pev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PPL_ECUDA, "event timing failed");
+        }
+        ms[k] = t;
+    }
     return PPL_OK;
 }
 
@@ -948,7 +1015,9 @@ int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float*
     g.out.kind = EPI_F32; g.out.out = C; g.out.sm_lo = N; g.out.sn_lo = 1; g.out.alpha = 1.0f;
     g.bn = bn_for(N);
     int r = tc_gemm(g, flag, s);
-    if (r) return fail(nullptr, PPL_ECUDA, "tensor-core GEMM launch failed (%d)", r);
+    if (r)
+        return fail(nullptr, PPL_ECUDA, "tensor-core GEMM launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
+                    r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
     cudaError_t ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "%s", cudaGetErrorString(ce));
     unsigned int f = 0;

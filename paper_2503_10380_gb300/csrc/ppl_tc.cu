@@ -29,7 +29,8 @@ namespace {
 
 constexpr int TM = 128;               // rows of the accumulator tile (TMEM lanes)
 constexpr int KROW_BYTES = 128;       // one swizzle row: 64 bf16 or 32 fp32
-constexpr int SMEM_BUDGET = 200 * 1024;
+constexpr int SMEM_BUDGET = 200 * 1024;      // operand stages
+constexpr int SMEM_ATTR = 220 * 1024;        // dynamic smem opt-in (stages + alignment + barriers)
 constexpr unsigned long long WAIT_NS = 500ull * 1000ull * 1000ull;   // 0.5 s per wait
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -404,8 +405,13 @@ int tc_init_driver() {
     g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_ATTR) != cudaSuccess ||
+            cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_ATTR) != cudaSuccess) {
+            cudaGetLastError();
+            return -2;
+        }
         attr_done = true;
     }
     return 0;
@@ -450,13 +456,15 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
         mBl = mBh;
     }
     const size_t smem = (size_t)stage_bytes * p.stages + 1024 + 16 * p.stages + 64;
+    if (smem > (size_t)SMEM_ATTR) return -6;
     dim3 grid((g.M + TM - 1) / TM, (g.N + p.bn - 1) / p.bn, g.batch * p.ksplit);
     if (grid.y > 65535 || grid.z > 65535) return -4;
     if (split)
         k_tc_gemm<PPL_PREC_BF16X3><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
     else
         k_tc_gemm<PPL_PREC_TF32><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
-    return cudaGetLastError() == cudaSuccess ? 0 : -5;
+    const cudaError_t le = cudaGetLastError();
+    return le == cudaSuccess ? 0 : -(1000 + (int)le);
 }
 
 void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch, void* dst, long long plane_elems,
