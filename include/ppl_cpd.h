@@ -144,6 +144,10 @@ int ppl_cpd_set_tau(ppl_cpd* h, const double* tau);
  * ENOTREADY if profiling is off or no sweep has run. */
 int ppl_cpd_phase_ms(ppl_cpd* h, double* ms);
 
+/* The caller has written a new guess into its factor buffer (the layout of
+ * ppl_cpd_init): recompute the Gram matrices the solves use and reset lam to 1. */
+int ppl_cpd_factors_changed(ppl_cpd* h);
+
 /* Counters and the last sweep's scalars. */
 int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* stats);
 

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_set_tau.argtypes = [H, c_void_p]
     L.ppl_cpd_stats_get.argtypes = [H, POINTER(ppl_cpd_stats)]
     L.ppl_cpd_phase_ms.argtypes = [H, POINTER(c_double)]
+    L.ppl_cpd_factors_changed.argtypes = [H]
     L.ppl_last_error.argtypes = [H]
     L.ppl_last_error.restype = c_char_p
     L.ppl_cpd_destroy.argtypes = [H]
@@ -73,7 +74,7 @@ def lib() -> ctypes.CDLL:
                               c_void_p]
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
-                 "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms",
+                 "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -146,6 +147,10 @@ def ppl_exact_contract(h, R_ptr=None):
 
 def ppl_cpd_set_tau(h, tau_ptr):
     _check(lib().ppl_cpd_set_tau(h, tau_ptr), h)
+
+
+def ppl_cpd_factors_changed(h):
+    _check(lib().ppl_cpd_factors_changed(h), h)
 
 
 def ppl_cpd_stats_get(h) -> dict:
@@ -249,6 +254,13 @@ class CpAls:
     def set_tau(self, tau):
         self.tau = tau.contiguous()
         ppl_cpd_set_tau(self.h, self.tau.data_ptr())
+
+    def set_factors(self, factors: dict):
+        """Write a new guess into the factor buffer and tell the library."""
+        f = self.factors()
+        for m in ("a", "b", "i", "j"):
+            f[m].copy_(self.torch.as_tensor(factors[m], dtype=self.torch.float64))
+        ppl_cpd_factors_changed(self.h)
 
     def stats(self) -> dict:
         return ppl_cpd_stats_get(self.h)

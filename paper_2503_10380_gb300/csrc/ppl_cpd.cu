@@ -539,8 +539,10 @@ void cross_gram(ppl_cpd* h, int m) {
     gemm64(g, h->st);
 }
 
+// phase boundary; External makes the record a real event node when the
+// sweep is being captured into a graph
 void mark(ppl_cpd* h, int k) {
-    if (h->opts.profile) cudaEventRecord(h->pev[k], h->st);
+    if (h->opts.profile) cudaEventRecordWithFlags(h->pev[k], h->st, cudaEventRecordExternal);
 }
 
 int sweep_body(ppl_cpd* h) {
@@ -924,6 +926,22 @@ int ppl_cpd_set_tau(ppl_cpd* h, const double* tau) {
         h->graph = nullptr;
         h->graph_ready = false;
     }
+    return e;
+}
+
+int ppl_cpd_factors_changed(ppl_cpd* h) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    int e = enter(h);
+    if (e) return e;
+    fill_f64(h->lam, (size_t)h->R, 1.0, h->st);
+    for (int m = 0; m < 4; ++m) gram(h, m);
+    fit_terms(h->at<double>(h->L.M), h->U[0], h->lam, 0, h->R, h->G(0), h->G(1), h->G(2), h->G(3),
+              h->at<double>(h->L.partial), h->scal() + SC_TERMS, h->st);
+    cudaMemcpyAsync(h->scal() + SC_NORM2_PREV, h->scal() + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice,
+                    h->st);
+    e = check_cuda(h, "factors_changed");
+    if (!e) e = sync_and_check(h);
+    leave(h);
     return e;
 }
 

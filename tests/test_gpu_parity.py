@@ -173,3 +173,17 @@ def test_errors_are_reported_not_raised_in_c():
         binding.ppl_cpd_mttkrp(cp.h, 7, 0)
     assert e.value.code == binding.PPL_EINVAL
     cp.close()
+
+
+def test_factors_changed_restarts_from_new_guess():
+    inp = inputs.make_inputs(3, 12, 20, 10, seed=8)
+    other = inputs.make_factors(99, 3, 12, 10)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="fp64")
+    cp.sweep(2)
+    cp.set_factors(other)
+    cp.sweep(2)
+    U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, other, 2)
+    f = {k: t.cpu().numpy() for k, t in cp.factors().items()}
+    for m in orc.MODES:
+        assert _rel(f[m], U_ref[m]) < 1e-9
+    cp.close()
