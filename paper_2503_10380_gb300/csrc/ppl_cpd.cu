@@ -250,19 +250,20 @@ void gram(ppl_cpd* h, int m) {
 }
 
 // solve the normal equations of mode m from M (in L.M), update U[m], lam, G[m]
-void solve_mode(ppl_cpd* h, int m) {
+int solve_mode(ppl_cpd* h, int m) {
     const int R = h->R, dim = h->dim(m);
     int oth[3], k = 0;
     for (int q = 0; q < 4; ++q)
         if (q != m) oth[k++] = q;
-    double* V = h->at<double>(h->L.V);
-    double* Z = h->at<double>(h->L.Z);
-    hadamard3(h->G(oth[0]), h->G(oth[1]), h->G(oth[2]), R, V, h->scal() + SC_TOL, h->st);
-    cholesky_blocked(V, R, h->at<double>(h->L.Linv), h->scal() + SC_TOL, h->nclamp(), h->st);
-    cudaMemcpyAsync(Z, h->at<double>(h->L.M), (size_t)dim * R * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
-    chol_solve_right(V, h->at<double>(h->L.Linv), R, Z, dim, h->st);
-    normalise_cols(Z, dim, R, h->U[m], h->lam, h->st);
-    gram(h, m);
+    char* f = h->ws + h->L.flags;
+    const int r = solve_mode_coop(h->G(oth[0]), h->G(oth[1]), h->G(oth[2]), h->at<double>(h->L.M), dim, R,
+                                  h->at<double>(h->L.V), h->at<double>(h->L.Linv), h->at<double>(h->L.Z), h->U[m],
+                                  h->lam, h->G(m), reinterpret_cast<unsigned int*>(f + 16),
+                                  reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(), h->st);
+    if (r != 0)
+        return fail(h, PPL_ECUDA, "cooperative solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
+                    r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
+    return PPL_OK;
 }
 
 // ---- MTTKRP, FP64 form --------------------------------------------------------
@@ -563,11 +564,11 @@ int sweep_body(ppl_cpd* h) {
         mark(h, 1);
         if ((e = chain_tc(h, 0, M))) return e;
         mark(h, 2);
-        solve_mode(h, 0);
+        if ((e = solve_mode(h, 0))) return e;
         mark(h, 3);
         if ((e = chain_tc(h, 1, M))) return e;
         mark(h, 4);
-        solve_mode(h, 1);
+        if ((e = solve_mode(h, 1))) return e;
         mark(h, 5);
         if ((e = p_tc(h))) return e;
     } else {
@@ -575,20 +576,20 @@ int sweep_body(ppl_cpd* h) {
         mark(h, 1);
         mttkrp_ab_fp64(h, 0, M);
         mark(h, 2);
-        solve_mode(h, 0);
+        if ((e = solve_mode(h, 0))) return e;
         mark(h, 3);
         mttkrp_ab_fp64(h, 1, M);
         mark(h, 4);
-        solve_mode(h, 1);
+        if ((e = solve_mode(h, 1))) return e;
         mark(h, 5);
         p_fp64(h);
     }
     mark(h, 6);
     double* P = h->at<double>(h->L.P);
     occ_mttkrp(P, R, h->U[3], o, R, 0, M, h->st);
-    solve_mode(h, 2);
+    if ((e = solve_mode(h, 2))) return e;
     occ_mttkrp(P, R, h->U[2], o, R, 1, M, h->st);
-    solve_mode(h, 3);
+    if ((e = solve_mode(h, 3))) return e;
     mark(h, 7);
     double* sc = h->scal();
     fit_terms(M, h->U[3], h->lam, o, R, h->G(0), h->G(1), h->G(2), h->G(3), h->at<double>(h->L.partial),

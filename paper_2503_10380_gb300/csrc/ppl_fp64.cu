@@ -130,60 +130,6 @@ __global__ void k_diag_tol(const double* V, int R, double* tol) {
     if (threadIdx.x == 0) tol[0] = fmax(ldexp(1.0, -52) * (double)R * red[0], 1e-300);
 }
 
-constexpr int CNB = 32;
-
-// Factor the kb x kb diagonal block at (k0, k0) of V (already updated by the
-// earlier panels) in shared memory, right-looking, pivots clamped at *tolp;
-// write L back and the block inverse L^-1 to Linv (row-major, 32 x 32).
-__global__ void __launch_bounds__(256) k_chol_diag(double* V, int ld, int k0, int kb, double* Linv,
-                                                   const double* tolp, unsigned long long* nclamp) {
-    __shared__ double L[CNB][CNB + 1];
-    __shared__ double Li[CNB][CNB + 1];
-    const int t = threadIdx.x;
-    const double tol = *tolp;
-    for (int e = t; e < CNB * CNB; e += blockDim.x) {
-        const int i = e / CNB, j = e % CNB;
-        L[i][j] = (i < kb && j <= i) ? V[(long long)(k0 + i) * ld + k0 + j] : 0.0;
-        Li[i][j] = 0.0;
-    }
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-        if (t == 0) {
-            double d = L[j][j];
-            if (!(d > tol)) {
-                d = tol;
-                atomicAdd(nclamp, 1ull);
-            }
-            L[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        const double piv = L[j][j];
-        for (int i = j + 1 + t; i < kb; i += blockDim.x) L[i][j] /= piv;
-        __syncthreads();
-        const int n = kb - j - 1;
-        for (int e = t; e < n * n; e += blockDim.x) {
-            const int i = j + 1 + e / n, c = j + 1 + e % n;
-            if (c <= i) L[i][c] -= L[i][j] * L[c][j];
-        }
-        __syncthreads();
-    }
-    for (int e = t; e < kb * kb; e += blockDim.x) {
-        const int i = e / kb, j = e % kb;
-        if (j <= i) V[(long long)(k0 + i) * ld + k0 + j] = L[i][j];
-    }
-    if (t < kb) {
-        const int c = t;
-        Li[c][c] = 1.0 / L[c][c];
-        for (int i = c + 1; i < kb; ++i) {
-            double s = 0.0;
-            for (int k = c; k < i; ++k) s = fma(L[i][k], Li[k][c], s);
-            Li[i][c] = -s / L[i][i];
-        }
-    }
-    __syncthreads();
-    for (int e = t; e < CNB * CNB; e += blockDim.x) Linv[e] = Li[e / CNB][e % CNB];
-}
-
 __global__ void k_normalise(const double* Ut, int dim, int R, double* U, double* lam) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
@@ -369,67 +315,6 @@ void kr_build_f64(const double* Ui, const double* Uj, int o, int R, double* KR, 
 void hadamard3(const double* G1, const double* G2, const double* G3, int R, double* V, double* tol, cudaStream_t s) {
     k_hadamard3<<<grid_for((long long)R * R, 256), 256, 0, s>>>(G1, G2, G3, R, V);
     k_diag_tol<<<1, 256, 0, s>>>(V, R, tol);
-}
-
-void cholesky_blocked(double* V, int R, double* Linv, const double* tol, unsigned long long* nclamp, cudaStream_t s) {
-    const int nt = (R + CNB - 1) / CNB;
-    for (int k = 0; k < nt; ++k) {
-        const int k0 = k * CNB, kb = (R - k0 < CNB) ? R - k0 : CNB;
-        k_chol_diag<<<1, 256, 0, s>>>(V, R, k0, kb, Linv + (size_t)k * CNB * CNB, tol, nclamp);
-        const int rest = R - k0 - kb;
-        if (rest <= 0) continue;
-        G64 p{};
-        p.A = V + (long long)(k0 + kb) * R + k0; p.am = ix1(R); p.ak = ix1(1);
-        p.B = Linv + (size_t)k * CNB * CNB; p.bn = ix1(CNB); p.bk = ix1(1);
-        p.C = V + (long long)(k0 + kb) * R + k0; p.cm = ix1(R); p.cn = ix1(1);
-        p.M = rest; p.N = kb; p.K = kb; p.batch = 1; p.ksplit = 1; p.alpha = 1.0; p.beta = 0.0;
-        gemm64(p, s);
-        G64 t{};
-        t.A = V + (long long)(k0 + kb) * R + k0; t.am = ix1(R); t.ak = ix1(1);
-        t.B = t.A; t.bn = ix1(R); t.bk = ix1(1);
-        t.C = V + (long long)(k0 + kb) * R + k0 + kb; t.cm = ix1(R); t.cn = ix1(1);
-        t.M = rest; t.N = rest; t.K = kb; t.batch = 1; t.ksplit = 1; t.alpha = -1.0; t.beta = 1.0; t.lower = 1;
-        gemm64(t, s);
-    }
-}
-
-void chol_solve_right(const double* L, const double* Linv, int R, double* Z, int dim, cudaStream_t s) {
-    const int nt = (R + CNB - 1) / CNB;
-    // Z <- Z L^-T, column block by column block (forward)
-    for (int k = 0; k < nt; ++k) {
-        const int k0 = k * CNB, kb = (R - k0 < CNB) ? R - k0 : CNB;
-        G64 d{};
-        d.A = Z + k0; d.am = ix1(R); d.ak = ix1(1);
-        d.B = Linv + (size_t)k * CNB * CNB; d.bn = ix1(CNB); d.bk = ix1(1);
-        d.C = Z + k0; d.cm = ix1(R); d.cn = ix1(1);
-        d.M = dim; d.N = kb; d.K = kb; d.batch = 1; d.ksplit = 1; d.alpha = 1.0;
-        gemm64(d, s);
-        const int rest = R - k0 - kb;
-        if (rest <= 0) continue;
-        G64 u{};
-        u.A = Z + k0; u.am = ix1(R); u.ak = ix1(1);
-        u.B = L + (long long)(k0 + kb) * R + k0; u.bn = ix1(R); u.bk = ix1(1);
-        u.C = Z + k0 + kb; u.cm = ix1(R); u.cn = ix1(1);
-        u.M = dim; u.N = rest; u.K = kb; u.batch = 1; u.ksplit = 1; u.alpha = -1.0; u.beta = 1.0;
-        gemm64(u, s);
-    }
-    // Z <- Z L^-1 (backward)
-    for (int k = nt - 1; k >= 0; --k) {
-        const int k0 = k * CNB, kb = (R - k0 < CNB) ? R - k0 : CNB;
-        G64 d{};
-        d.A = Z + k0; d.am = ix1(R); d.ak = ix1(1);
-        d.B = Linv + (size_t)k * CNB * CNB; d.bn = ix1(1); d.bk = ix1(CNB);
-        d.C = Z + k0; d.cm = ix1(R); d.cn = ix1(1);
-        d.M = dim; d.N = kb; d.K = kb; d.batch = 1; d.ksplit = 1; d.alpha = 1.0;
-        gemm64(d, s);
-        if (k0 == 0) continue;
-        G64 u{};
-        u.A = Z + k0; u.am = ix1(R); u.ak = ix1(1);
-        u.B = L + (long long)k0 * R; u.bn = ix1(1); u.bk = ix1(R);
-        u.C = Z; u.cm = ix1(R); u.cn = ix1(1);
-        u.M = dim; u.N = k0; u.K = kb; u.batch = 1; u.ksplit = 1; u.alpha = -1.0; u.beta = 1.0;
-        gemm64(u, s);
-    }
 }
 
 void normalise_cols(const double* Ut, int dim, int R, double* U, double* lam, cudaStream_t s) {

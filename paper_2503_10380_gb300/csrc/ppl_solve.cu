@@ -1,0 +1,409 @@
+// One ALS mode update in a single cooperative FP64 kernel (Optimizing the
+// CP-PPL tensor-network section: W as the Hadamard product of the other
+// three Gram matrices, a Cholesky solve of the normal equations, column
+// normalisation; then the new factor's Gram matrix for the next updates).
+//
+//   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, tol = max(2^-52 R max V_kk, 1e-300)
+//   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol)
+//       with the rows of Z appended below V, so the same panel and trailing
+//       updates carry out the forward substitution Z <- M L^-T
+//   P2  backward substitution Z <- Z L^-1, block column by block column
+//   P3  lam_r = ||Z[:, r]||, U = Z / lam (a zero column keeps lam = 0)
+//   P4  G = U^T U
+//
+// GB300 executes about two FP64 FMAs per clock per SM, so every phase is
+// spread over all SMs in 32 x 32 tiles and 8-row panels; phases are separated
+// by grid barriers (a cooperative launch guarantees co-residency).  Every
+// barrier wait is bounded: on expiry the kernel raises an abort flag that
+// all blocks observe, records the error and returns.
+#include "ppl_internal.h"
+
+#include <cmath>
+
+namespace {
+
+constexpr int NB = 32;
+constexpr int NT = 256;
+constexpr unsigned long long BAR_NS = 1000ull * 1000ull * 1000ull;   // 1 s per barrier wait
+
+struct SolveP {
+    const double* G1;
+    const double* G2;
+    const double* G3;
+    double* V;
+    double* Linv;
+    const double* M;
+    double* Z;
+    double* U;
+    double* lam;
+    double* G;
+    unsigned int* sync;              // [0] arrivals, [1] generation, [2] abort
+    unsigned long long* maxdiag;
+    unsigned long long* nclamp;
+    unsigned int* err;
+    int R, dim;
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_vol(const unsigned int* p) { return *(volatile const unsigned int*)p; }
+
+// grid-wide barrier; false when the wait expired or another block aborted
+__device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&p.sync[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&p.sync[0], 0u);
+            __threadfence();
+            atomicAdd(&p.sync[1], 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            while (ld_vol(&p.sync[1]) == gen) {
+                if (ld_vol(&p.sync[2])) {
+                    ok = 0;
+                    break;
+                }
+                if (gtimer() - t0 > BAR_NS) {
+                    atomicExch(&p.sync[2], 1u);
+                    atomicOr(p.err, 16u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        gen += 1;
+        if (ld_vol(&p.sync[2])) ok = 0;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__device__ __forceinline__ void tri_index(int t, int& I, int& J) {
+    // t -> (I, J), I >= J, row-major over the lower triangle
+    int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    I = i;
+    J = t - i * (i + 1) / 2;
+}
+
+// Factor the kb x kb diagonal block held in Ls (lower) in place, clamping
+// pivots at tol, and form its inverse in Li (lower).  All 256 threads.
+__device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], int kb, double tol, bool count,
+                            unsigned long long* nclamp, double* s_inv) {
+    const int t = threadIdx.x;
+    for (int j = 0; j < kb; ++j) {
+        if (t == 0) {
+            double d = Ls[j][j];
+            if (!(d > tol)) {
+                d = tol;
+                if (count) atomicAdd(nclamp, 1ull);
+            }
+            const double s = sqrt(d);
+            Ls[j][j] = s;
+            *s_inv = 1.0 / s;
+        }
+        __syncthreads();
+        const double inv = *s_inv;
+        if (t > j && t < kb) Ls[t][j] *= inv;
+        __syncthreads();
+        const int n = kb - j - 1;
+        for (int e = t; e < n * n; e += NT) {
+            const int i = j + 1 + e / n, c = j + 1 + e % n;
+            if (c <= i) Ls[i][c] = fma(-Ls[i][j], Ls[c][j], Ls[i][c]);
+        }
+        __syncthreads();
+    }
+    // inverse, column c by 8 threads: Li[i][c] = -(sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
+    const int c = t / 8, q = t % 8;
+    for (int e = t; e < NB * (NB + 1); e += NT) (&Li[0][0])[e] = 0.0;
+    __syncthreads();
+    if (c < kb && q == 0) Li[c][c] = 1.0 / Ls[c][c];
+    __syncthreads();
+    for (int i = 1; i < kb; ++i) {
+        double s = 0.0;
+        if (c < i) {
+            for (int k = c + q; k < i; k += 8) s = fma(Ls[i][k], Li[k][c], s);
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        if (c < i && q == 0) Li[i][c] = -s / Ls[i][i];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double Li[NB][NB + 1];
+    __shared__ double Ta[NB][NB + 1];
+    __shared__ double Tb[NB][NB + 1];
+    __shared__ double s_inv;
+    __shared__ int s_flag;
+    __shared__ unsigned int s_gen;
+
+    const int R = p.R, dim = p.dim;
+    const int tid = threadIdx.x;
+    const long long gtid = (long long)blockIdx.x * NT + tid;
+    const long long gthreads = (long long)gridDim.x * NT;
+    if (tid == 0) s_gen = ld_vol(&p.sync[1]);
+    __syncthreads();
+    unsigned int gen = s_gen;   // meaningful in thread 0 only
+
+    // ---- P0 --------------------------------------------------------------------
+    for (long long e = gtid; e < (long long)R * R; e += gthreads) {
+        const int r = (int)(e / R), q = (int)(e % R);
+        if (q <= r) {
+            const double x = p.G1[e] * p.G2[e] * p.G3[e];
+            p.V[e] = x;
+            if (q == r) atomicMax(p.maxdiag, (unsigned long long)__double_as_longlong(fmax(x, 0.0)));
+        }
+    }
+    for (long long e = gtid; e < (long long)dim * R; e += gthreads) p.Z[e] = p.M[e];
+    if (!gsync(p, gen, &s_flag)) return;
+    const double tol = fmax(ldexp(1.0, -52) * (double)R * __longlong_as_double((long long)__ldcg(p.maxdiag)), 1e-300);
+
+    const int nt = (R + NB - 1) / NB;
+    const int D = (dim + NB - 1) / NB;
+    const int tx = tid % 16, ty = tid / 16;
+
+    // ---- P1: Cholesky with the forward substitution fused ------------------------
+    for (int k = 0; k < nt; ++k) {
+        const int k0 = k * NB, kb = min(NB, R - k0);
+        for (int e = tid; e < NB * NB; e += NT) {
+            const int i = e / NB, j = e % NB;
+            Ls[i][j] = (i < kb && j <= i) ? __ldcg(p.V + (long long)(k0 + i) * R + k0 + j) : 0.0;
+        }
+        __syncthreads();
+        diag_factor(Ls, Li, kb, tol, blockIdx.x == 0, p.nclamp, &s_inv);
+        if (blockIdx.x == 0) {
+            for (int e = tid; e < kb * kb; e += NT) {
+                const int i = e / kb, j = e % kb;
+                if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
+            }
+            for (int e = tid; e < NB * NB; e += NT) p.Linv[(long long)k * NB * NB + e] = Li[e / NB][e % NB];
+        }
+        // panel: rows below the block (V) and all rows of Z, 8 rows per task
+        const int vrows = R - k0 - kb;
+        const int prow = vrows + dim;
+        const int ntask = (prow + 7) / 8;
+        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+            const int rr = task * 8 + tid / NB, t = tid % NB;
+            double* row = nullptr;
+            if (rr < prow) row = (rr < vrows) ? p.V + (long long)(k0 + kb + rr) * R + k0 : p.Z + (long long)(rr - vrows) * R + k0;
+            Ta[tid / NB][t] = (row && t < kb) ? __ldcg(row + t) : 0.0;
+            __syncthreads();
+            if (row && t < kb) {
+                double s = 0.0;
+                for (int q = 0; q <= t; ++q) s = fma(Ta[tid / NB][q], Li[t][q], s);
+                row[t] = s;
+            }
+            __syncthreads();
+        }
+        if (!gsync(p, gen, &s_flag)) return;
+        // trailing update of V (lower tiles) and of Z
+        const int Tk = (vrows + NB - 1) / NB;
+        const int ntri = Tk * (Tk + 1) / 2;
+        const int ntile = ntri + D * Tk;
+        for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+            const double* Pa;
+            int arows, i0;
+            double* C;
+            int j0;
+            if (tile < ntri) {
+                int I, J;
+                tri_index(tile, I, J);
+                i0 = k0 + kb + I * NB;
+                j0 = k0 + kb + J * NB;
+                Pa = p.V + (long long)i0 * R + k0;
+                arows = R - i0;
+                C = p.V + (long long)i0 * R + j0;
+            } else {
+                const int tz = tile - ntri;
+                const int Mb = tz / Tk, J = tz % Tk;
+                i0 = Mb * NB;
+                j0 = k0 + kb + J * NB;
+                Pa = p.Z + (long long)i0 * R + k0;
+                arows = dim - i0;
+                C = p.Z + (long long)i0 * R + j0;
+            }
+            const int brows = R - j0;
+            const double* Pb = p.V + (long long)j0 * R + k0;
+            for (int e = tid; e < NB * NB; e += NT) {
+                const int i = e / NB, s = e % NB;
+                Ta[i][s] = (i < arows && s < kb) ? __ldcg(Pa + (long long)i * R + s) : 0.0;
+                Tb[i][s] = (i < brows && s < kb) ? __ldcg(Pb + (long long)i * R + s) : 0.0;
+            }
+            __syncthreads();
+            double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+            for (int s = 0; s < kb; ++s) {
+                const double x0 = Ta[ty][s], x1 = Ta[ty + 16][s];
+                const double y0 = Tb[tx][s], y1 = Tb[tx + 16][s];
+                a00 = fma(x0, y0, a00);
+                a01 = fma(x0, y1, a01);
+                a10 = fma(x1, y0, a10);
+                a11 = fma(x1, y1, a11);
+            }
+            const double acc[2][2] = {{a00, a01}, {a10, a11}};
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    const int i = ty + 16 * a, j = tx + 16 * b;
+                    if (i < arows && j < brows) {
+                        double* c = C + (long long)i * R + j;
+                        *c = __ldcg(c) - acc[a][b];
+                    }
+                }
+            __syncthreads();
+        }
+        if (!gsync(p, gen, &s_flag)) return;
+    }
+
+    // ---- P2: backward substitution Z <- Z L^-1 -------------------------------------
+    for (int k = nt - 1; k >= 0; --k) {
+        const int k0 = k * NB, kb = min(NB, R - k0);
+        for (int e = tid; e < NB * NB; e += NT) Li[e / NB][e % NB] = __ldcg(p.Linv + (long long)k * NB * NB + e);
+        __syncthreads();
+        const int ntask = (dim + 7) / 8;
+        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+            const int rr = task * 8 + tid / NB, t = tid % NB;
+            double* row = (rr < dim) ? p.Z + (long long)rr * R + k0 : nullptr;
+            Ta[tid / NB][t] = (row && t < kb) ? __ldcg(row + t) : 0.0;
+            __syncthreads();
+            if (row && t < kb) {
+                double s = 0.0;
+                for (int q = t; q < kb; ++q) s = fma(Ta[tid / NB][q], Li[q][t], s);
+                row[t] = s;
+            }
+            __syncthreads();
+        }
+        if (!gsync(p, gen, &s_flag)) return;
+        if (k > 0) {
+            const int ntile = D * k;
+            for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+                const int Mb = tile / k, J = tile % k;
+                const int i0 = Mb * NB, j0 = J * NB;
+                const int arows = dim - i0;
+                for (int e = tid; e < NB * NB; e += NT) {
+                    const int i = e / NB, s = e % NB;
+                    Ta[i][s] = (i < arows && s < kb) ? __ldcg(p.Z + (long long)(i0 + i) * R + k0 + s) : 0.0;
+                    Tb[i][s] = (i < kb) ? __ldcg(p.V + (long long)(k0 + i) * R + j0 + s) : 0.0;   // Tb[t][j] = L[k0+t][j0+j]
+                }
+                __syncthreads();
+                double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+                for (int s = 0; s < kb; ++s) {
+                    const double x0 = Ta[ty][s], x1 = Ta[ty + 16][s];
+                    const double y0 = Tb[s][tx], y1 = Tb[s][tx + 16];
+                    a00 = fma(x0, y0, a00);
+                    a01 = fma(x0, y1, a01);
+                    a10 = fma(x1, y0, a10);
+                    a11 = fma(x1, y1, a11);
+                }
+                const double acc[2][2] = {{a00, a01}, {a10, a11}};
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        const int i = ty + 16 * a, j = tx + 16 * b;
+                        if (i < arows) {
+                            double* c = p.Z + (long long)(i0 + i) * R + j0 + j;
+                            *c = __ldcg(c) - acc[a][b];
+                        }
+                    }
+                __syncthreads();
+            }
+        }
+        if (!gsync(p, gen, &s_flag)) return;
+    }
+
+    // ---- P3: normalise -------------------------------------------------------------
+    for (long long r = gtid; r < R; r += gthreads) {
+        double s = 0.0;
+        for (int x = 0; x < dim; ++x) {
+            const double u = __ldcg(p.Z + (long long)x * R + r);
+            s = fma(u, u, s);
+        }
+        const double l = sqrt(s);
+        const double inv = (l > 0.0) ? 1.0 / l : 1.0;
+        for (int x = 0; x < dim; ++x) p.U[(long long)x * R + r] = __ldcg(p.Z + (long long)x * R + r) * inv;
+        p.lam[r] = l;
+    }
+    if (!gsync(p, gen, &s_flag)) return;
+
+    // ---- P4: Gram of the new factor -------------------------------------------------
+    const int TR = (R + NB - 1) / NB;
+    const int ntri = TR * (TR + 1) / 2;
+    for (int tile = blockIdx.x; tile < ntri; tile += gridDim.x) {
+        int I, J;
+        tri_index(tile, I, J);
+        const int i0 = I * NB, j0 = J * NB;
+        double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+        for (int x0 = 0; x0 < dim; x0 += NB) {
+            for (int e = tid; e < NB * NB; e += NT) {
+                const int x = e / NB, c = e % NB;
+                const bool okx = (x0 + x < dim);
+                Ta[x][c] = (okx && i0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + i0 + c) : 0.0;
+                Tb[x][c] = (okx && j0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + j0 + c) : 0.0;
+            }
+            __syncthreads();
+            for (int x = 0; x < NB; ++x) {
+                const double u0 = Ta[x][ty], u1 = Ta[x][ty + 16];
+                const double w0 = Tb[x][tx], w1 = Tb[x][tx + 16];
+                a00 = fma(u0, w0, a00);
+                a01 = fma(u0, w1, a01);
+                a10 = fma(u1, w0, a10);
+                a11 = fma(u1, w1, a11);
+            }
+            __syncthreads();
+        }
+        const double acc[2][2] = {{a00, a01}, {a10, a11}};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+                if (i < R && j < R) {
+                    p.G[(long long)i * R + j] = acc[a][b];
+                    p.G[(long long)j * R + i] = acc[a][b];
+                }
+            }
+    }
+}
+
+int g_solve_grid = 0;
+
+}  // namespace
+
+int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
+                    double* V, double* Linv, double* Z, double* U, double* lam, double* G, unsigned int* sync,
+                    unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err, cudaStream_t s) {
+    if (g_solve_grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve, NT, 0);
+        if (sms <= 0 || per <= 0) return -1;
+        g_solve_grid = sms * (per < 2 ? per : 2);
+    }
+    cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
+    cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
+    SolveP p;
+    p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.U = U; p.lam = lam; p.G = G;
+    p.sync = sync; p.maxdiag = maxdiag; p.nclamp = nclamp; p.err = err; p.R = R; p.dim = dim;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_solve_grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve, p);
+    return e == cudaSuccess ? 0 : -(1000 + (int)e);
+}
