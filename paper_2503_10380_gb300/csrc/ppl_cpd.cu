@@ -41,7 +41,7 @@ struct Layout {
 constexpr int NPART = 2 * 304 + 8;
 constexpr int NSCAL = 64;
 // scalar slots
-constexpr int SC_TOL = 0, SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
+constexpr int SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
               SC_EXACT = 14;
 
 bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {

@@ -97,37 +97,48 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
 }
 
 // Factor the kb x kb diagonal block held in Ls (lower) in place, clamping
-// pivots at tol, and form its inverse in Li (lower).  All 256 threads.
-__device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], int kb, double tol, bool count,
-                            unsigned long long* nclamp, double* s_inv) {
+// pivots at tol, and form its inverse in Li (lower).  All NT threads.
+// Right-looking on unscaled columns: with d_j the (clamped) pivot,
+// A[i][c] -= A[i][j] A[c][j] / d_j, so a column costs one division; the
+// square roots and column scalings are applied in one parallel pass at the end.
+__device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* rd, int kb, double tol,
+                            unsigned long long* nclamp) {
     const int t = threadIdx.x;
     for (int j = 0; j < kb; ++j) {
         if (t == 0) {
             double d = Ls[j][j];
             if (!(d > tol)) {
                 d = tol;
-                if (count) atomicAdd(nclamp, 1ull);
+                atomicAdd(nclamp, 1ull);
             }
-            const double s = sqrt(d);
-            Ls[j][j] = s;
-            *s_inv = 1.0 / s;
+            Ls[j][j] = d;
+            rd[j] = 1.0 / d;
         }
         __syncthreads();
-        const double inv = *s_inv;
-        if (t > j && t < kb) Ls[t][j] *= inv;
-        __syncthreads();
         const int n = kb - j - 1;
+        const double r = rd[j];
         for (int e = t; e < n * n; e += NT) {
-            const int i = j + 1 + e / n, c = j + 1 + e % n;
-            if (c <= i) Ls[i][c] = fma(-Ls[i][j], Ls[c][j], Ls[i][c]);
+            const int ii = j + 1 + e / n, cc = j + 1 + e % n;
+            if (cc <= ii) Ls[ii][cc] = fma(-Ls[ii][j] * r, Ls[cc][j], Ls[ii][cc]);
         }
         __syncthreads();
     }
-    // inverse, column c by 8 threads: Li[i][c] = -(sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
-    const int c = t / 8, q = t % 8;
+    // L = A_unscaled * diag(1/sqrt(d)), L_jj = sqrt(d_j); rd <- 1 / L_jj
+    if (t < kb) {
+        const double sd = sqrt(Ls[t][t]);
+        rd[t] = 1.0 / sd;
+        Ls[t][t] = sd;
+    }
+    __syncthreads();
+    for (int e = t; e < kb * kb; e += NT) {
+        const int i = e / kb, j = e % kb;
+        if (j < i) Ls[i][j] *= rd[j];
+    }
     for (int e = t; e < NB * (NB + 1); e += NT) (&Li[0][0])[e] = 0.0;
     __syncthreads();
-    if (c < kb && q == 0) Li[c][c] = 1.0 / Ls[c][c];
+    // inverse, column c by 8 threads: Li[i][c] = -(sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
+    const int c = t / 8, q = t % 8;
+    if (c < kb && q == 0) Li[c][c] = rd[c];
     __syncthreads();
     for (int i = 1; i < kb; ++i) {
         double s = 0.0;
@@ -137,9 +148,30 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], int kb, 
         s += __shfl_xor_sync(0xffffffffu, s, 1);
         s += __shfl_xor_sync(0xffffffffu, s, 2);
         s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if (c < i && q == 0) Li[i][c] = -s / Ls[i][i];
+        if (c < i && q == 0) Li[i][c] = -s * rd[i];
         __syncthreads();
     }
+}
+
+// load the lower kb x kb block of V at (k0, k0) into Ls, factor it, write L
+// back to V and L^-1 to Linv[k]
+__device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB + 1], double (*Li)[NB + 1],
+                             double* rd) {
+    const int R = p.R, tid = threadIdx.x;
+    const int k0 = k * NB, kb = min(NB, R - k0);
+    for (int e = tid; e < NB * NB; e += NT) {
+        const int i = e / NB, j = e % NB;
+        Ls[i][j] = (i < kb && j <= i) ? __ldcg(p.V + (long long)(k0 + i) * R + k0 + j) : 0.0;
+    }
+    __syncthreads();
+    diag_factor(Ls, Li, rd, kb, tol, p.nclamp);
+    for (int e = tid; e < kb * kb; e += NT) {
+        const int i = e / kb, j = e % kb;
+        if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
+    }
+    for (int e = tid; e < NB * NB; e += NT) p.Linv[(long long)k * NB * NB + e] = Li[e / NB][e % NB];
+    __threadfence();
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
@@ -147,7 +179,8 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     __shared__ double Li[NB][NB + 1];
     __shared__ double Ta[NB][NB + 1];
     __shared__ double Tb[NB][NB + 1];
-    __shared__ double s_inv;
+    __shared__ double rd[NB];
+    __shared__ double red[NT / 32];
     __shared__ int s_flag;
     __shared__ unsigned int s_gen;
 
@@ -158,45 +191,57 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     if (tid == 0) s_gen = ld_vol(&p.sync[1]);
     __syncthreads();
     unsigned int gen = s_gen;   // meaningful in thread 0 only
+    const int kb0 = min(NB, R);
 
     // ---- P0 --------------------------------------------------------------------
+    // every block forms the pivot tolerance from the diagonal of V itself
+    double mx = 0.0;
+    for (int i = tid; i < R; i += NT) {
+        const long long d = (long long)i * R + i;
+        mx = fmax(mx, p.G1[d] * p.G2[d] * p.G3[d]);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (tid % 32 == 0) red[tid / 32] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < NT / 32; ++w) mx = fmax(mx, red[w]);
+    const double tol = fmax(ldexp(1.0, -52) * (double)R * mx, 1e-300);
+    __syncthreads();
     for (long long e = gtid; e < (long long)R * R; e += gthreads) {
         const int r = (int)(e / R), q = (int)(e % R);
-        if (q <= r) {
-            const double x = p.G1[e] * p.G2[e] * p.G3[e];
-            p.V[e] = x;
-            if (q == r) atomicMax(p.maxdiag, (unsigned long long)__double_as_longlong(fmax(x, 0.0)));
-        }
+        if (q <= r && !(r < kb0 && q < kb0)) p.V[e] = p.G1[e] * p.G2[e] * p.G3[e];
     }
     for (long long e = gtid; e < (long long)dim * R; e += gthreads) p.Z[e] = p.M[e];
+    if (blockIdx.x == 0) {
+        // the first diagonal block straight from the Gram matrices
+        for (int e = tid; e < kb0 * kb0; e += NT) {
+            const int i = e / kb0, j = e % kb0;
+            if (j <= i) {
+                const long long d = (long long)i * R + j;
+                p.V[d] = p.G1[d] * p.G2[d] * p.G3[d];
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        factor_block(p, 0, tol, Ls, Li, rd);
+    }
     if (!gsync(p, gen, &s_flag)) return;
-    const double tol = fmax(ldexp(1.0, -52) * (double)R * __longlong_as_double((long long)__ldcg(p.maxdiag)), 1e-300);
 
     const int nt = (R + NB - 1) / NB;
     const int D = (dim + NB - 1) / NB;
     const int tx = tid % 16, ty = tid / 16;
+    const int G = gridDim.x;
 
-    // ---- P1: Cholesky with the forward substitution fused ------------------------
+    // ---- P1: Cholesky with the forward substitution fused, one block of look-ahead
     for (int k = 0; k < nt; ++k) {
         const int k0 = k * NB, kb = min(NB, R - k0);
-        for (int e = tid; e < NB * NB; e += NT) {
-            const int i = e / NB, j = e % NB;
-            Ls[i][j] = (i < kb && j <= i) ? __ldcg(p.V + (long long)(k0 + i) * R + k0 + j) : 0.0;
-        }
+        for (int e = tid; e < NB * NB; e += NT) Li[e / NB][e % NB] = __ldcg(p.Linv + (long long)k * NB * NB + e);
         __syncthreads();
-        diag_factor(Ls, Li, kb, tol, blockIdx.x == 0, p.nclamp, &s_inv);
-        if (blockIdx.x == 0) {
-            for (int e = tid; e < kb * kb; e += NT) {
-                const int i = e / kb, j = e % kb;
-                if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
-            }
-            for (int e = tid; e < NB * NB; e += NT) p.Linv[(long long)k * NB * NB + e] = Li[e / NB][e % NB];
-        }
         // panel: rows below the block (V) and all rows of Z, 8 rows per task
         const int vrows = R - k0 - kb;
         const int prow = vrows + dim;
         const int ntask = (prow + 7) / 8;
-        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        for (int task = blockIdx.x; task < ntask; task += G) {
             const int rr = task * 8 + tid / NB, t = tid % NB;
             double* row = nullptr;
             if (rr < prow) row = (rr < vrows) ? p.V + (long long)(k0 + kb + rr) * R + k0 : p.Z + (long long)(rr - vrows) * R + k0;
@@ -210,11 +255,24 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             __syncthreads();
         }
         if (!gsync(p, gen, &s_flag)) return;
-        // trailing update of V (lower tiles) and of Z
+        // trailing update of V (lower tiles) and of Z.  Tile 0 is the next
+        // diagonal block: block 0 updates it and factors it while the other
+        // blocks take the remaining tiles.
         const int Tk = (vrows + NB - 1) / NB;
         const int ntri = Tk * (Tk + 1) / 2;
         const int ntile = ntri + D * Tk;
-        for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        int first, stride;
+        if (G == 1) {
+            first = 0;
+            stride = 1;
+        } else if (blockIdx.x == 0) {
+            first = 0;
+            stride = ntile + 1;   // tile 0 only
+        } else {
+            first = blockIdx.x;
+            stride = G - 1;
+        }
+        for (int tile = first; tile < ntile; tile += stride) {
             const double* Pa;
             int arows, i0;
             double* C;
@@ -239,15 +297,15 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             const int brows = R - j0;
             const double* Pb = p.V + (long long)j0 * R + k0;
             for (int e = tid; e < NB * NB; e += NT) {
-                const int i = e / NB, s = e % NB;
-                Ta[i][s] = (i < arows && s < kb) ? __ldcg(Pa + (long long)i * R + s) : 0.0;
-                Tb[i][s] = (i < brows && s < kb) ? __ldcg(Pb + (long long)i * R + s) : 0.0;
+                const int i = e / NB, s2 = e % NB;
+                Ta[i][s2] = (i < arows && s2 < kb) ? __ldcg(Pa + (long long)i * R + s2) : 0.0;
+                Tb[i][s2] = (i < brows && s2 < kb) ? __ldcg(Pb + (long long)i * R + s2) : 0.0;
             }
             __syncthreads();
             double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
-            for (int s = 0; s < kb; ++s) {
-                const double x0 = Ta[ty][s], x1 = Ta[ty + 16][s];
-                const double y0 = Tb[tx][s], y1 = Tb[tx + 16][s];
+            for (int s2 = 0; s2 < kb; ++s2) {
+                const double x0 = Ta[ty][s2], x1 = Ta[ty + 16][s2];
+                const double y0 = Tb[tx][s2], y1 = Tb[tx + 16][s2];
                 a00 = fma(x0, y0, a00);
                 a01 = fma(x0, y1, a01);
                 a10 = fma(x1, y0, a10);
@@ -257,12 +315,14 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b) {
                     const int i = ty + 16 * a, j = tx + 16 * b;
-                    if (i < arows && j < brows) {
+                    if (i < arows && j < brows && (tile >= ntri || i0 != j0 || j <= i)) {
                         double* c = C + (long long)i * R + j;
                         *c = __ldcg(c) - acc[a][b];
                     }
                 }
+            __threadfence();
             __syncthreads();
+            if (tile == 0 && k + 1 < nt) factor_block(p, k + 1, tol, Ls, Li, rd);
         }
         if (!gsync(p, gen, &s_flag)) return;
     }
@@ -387,7 +447,7 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve, NT, 0);
         if (sms <= 0 || per <= 0) return -1;
-        g_solve_grid = sms * (per < 2 ? per : 2);
+        g_solve_grid = sms;   // one block per SM: the look-ahead block keeps its SM's FP64 pipe
     }
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
