@@ -159,6 +159,30 @@ const char* ppl_last_error(const ppl_cpd* h);
  * frees its workspace, B, tau and factors.  h may be NULL. */
 int ppl_cpd_destroy(ppl_cpd* h);
 
+/* ---- allocation-free variant ----------------------------------------------------
+ * ppl_cp_energy_static: the CP energy of ppl_cpd_energy (same formula, FP64)
+ * for callers that cannot allocate device memory at the point of the call:
+ * code running inside a framework whose device memory is owned by its own
+ * pooling allocator and that has no way to hand a workspace through, or
+ * latency-bound code that must not call cudaMalloc / cudaFree (both can
+ * synchronise the whole device) in the middle of a solve.  The paper has no
+ * counterpart; this is a convenience of the library.
+ *
+ * Inputs are the same device arrays as ppl_cpd_init takes: B [X][o+v][o+v]
+ * and the factor buffer Ua | Ub | Ui | Uj | lam.  E_cp is a HOST double;
+ * the call synchronises `stream`.  Scratch is one array of
+ * PPL_STATIC_SCRATCH_BYTES in the library's device image, which every GPU
+ * that loads the library holds until the process exits; it requires
+ * 2 * o * R * 8 + 8448 <= PPL_STATIC_SCRATCH_BYTES (o * R <= 523760) and
+ * returns PPL_EINVAL otherwise.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (the call clears what it accumulates into): calls
+ * that overlap on the GPU, from several streams or threads, race. */
+#define PPL_STATIC_SCRATCH_BYTES (8u << 20)
+int ppl_cp_energy_static(int o, int v, int X, int R, const double* B, const double* factors,
+                         double* E_cp, void* stream);
+
 /* Building-block check of the tensor-core contraction used by the MTTKRP:
  * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the
  * given PPL_PREC_BF16X3 or PPL_PREC_TF32 tcgen05 kernel (operands split or

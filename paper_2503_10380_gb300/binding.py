@@ -72,6 +72,9 @@ def lib() -> ctypes.CDLL:
     L.ppl_tc_gemm_workspace_size.argtypes = [c_int, c_int, c_int, c_int, POINTER(c_size_t)]
     L.ppl_tc_gemm.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                               c_void_p]
+    L.ppl_cp_energy_static.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_void_p, POINTER(c_double),
+                                       c_void_p]
+    L.ppl_cp_energy_static.restype = c_int
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
@@ -170,6 +173,14 @@ def ppl_cpd_phase_ms(h) -> dict:
 
 def ppl_cpd_destroy(h):
     _check(lib().ppl_cpd_destroy(h))
+
+
+def ppl_cp_energy_static(o, v, X, R, B_ptr, factors_ptr, stream_ptr) -> float:
+    """CP energy without any device allocation (scratch is a static array in
+    the library); see include/ppl_cpd.h for the size limit and the sharing rules."""
+    E = c_double()
+    _check(lib().ppl_cp_energy_static(o, v, X, R, B_ptr, factors_ptr, ctypes.byref(E), stream_ptr))
+    return E.value
 
 
 def ppl_tc_gemm_workspace_size(M, N, K, precision) -> int:

@@ -16,7 +16,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
-SOURCES = ["ppl_fp64.cu", "ppl_tc.cu", "ppl_solve.cu", "ppl_cpd.cu"]
+SOURCES = ["ppl_fp64.cu", "ppl_tc.cu", "ppl_solve.cu", "ppl_cpd.cu", "ppl_static.cu"]
 LIB = os.path.join(PKG, "libpplcpd.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 

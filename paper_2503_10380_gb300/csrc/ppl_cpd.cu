@@ -634,6 +634,9 @@ int sync_and_check(ppl_cpd* h) {
 
 }  // namespace
 
+// message for ppl_last_error(NULL) from other translation units
+void ppl_set_global_error(const char* msg) { g_err = msg; }
+
 // ============================================================================
 // C ABI
 // ============================================================================
