@@ -207,7 +207,7 @@ def run_ours(args, world, rank, local):
     tau = tau_h.to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    cp = binding.CpAls(B, tau, inp.factors, precision=args.precision, profile=True)
+    cp = binding.CpAls(B, tau, inp.factors, precision=args.precision, profile=True, r_chunk=args.r_chunk)
     normR2, E_exact, _ = cp.exact_contract()
     for _ in range(args.warmup):
         cp.sweep(1, want_hist=False)
@@ -249,7 +249,7 @@ def run_ours(args, world, rank, local):
 
     # ---- accuracy and the plain FP64 GPU form from the same start -------------
     n_cmp = SWEEPS_PER_SOLVE
-    mixed = binding.CpAls(B, tau, inp.factors, precision=args.precision)
+    mixed = binding.CpAls(B, tau, inp.factors, precision=args.precision, r_chunk=args.r_chunk)
     mixed.set_normR2(normR2)
     fits_mixed = mixed.sweep(n_cmp)
     E_mixed = mixed.energy()
@@ -273,7 +273,7 @@ def run_ours(args, world, rank, local):
     # its operand copies rebuilt, SWEEPS_PER_SOLVE sweeps warm-started from the
     # factors already on the device, then factors and fit history read back.
     # B stays resident (the DF integrals do not change between CC iterations).
-    e2e = binding.CpAls(B, tau, inp.factors, precision=args.precision)
+    e2e = binding.CpAls(B, tau, inp.factors, precision=args.precision, r_chunk=args.r_chunk)
     e2e.set_normR2(normR2)
     fac_out = torch.empty(e2e.fac.numel(), dtype=torch.float64).pin_memory()
     tau_dev = e2e.tau
@@ -324,7 +324,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": args.precision,
         "data": "synthetic (seeded; shapes of the paper's molecules)",
         "config": {"workload": WORKLOAD, "o": O, "v": V, "X": XAUX, "R": RANK,
-                   "precision": args.precision, "l2": "inputs larger than L2 (tau, B operand planes ~0.5 GB)",
+                   "precision": args.precision, "r_chunk": args.r_chunk or "auto",
+                   "l2": "inputs larger than L2 (tau, B operand planes ~0.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mttkrp_tflops": mttkrp_tflops,
         "phase_ms": phases,
@@ -360,6 +361,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16x3", "tf32"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -31,7 +31,7 @@ struct Layout {
     // offsets (bytes) into the workspace; -1 = absent
     size_t G[4], V, Linv, Z, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
     size_t T64, W64, Y64, S64;                       // FP64 form
-    size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S;   // tensor-core form
+    size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Za, Zb, gov, Gblk, Rblk;
     size_t total;
     int rc, na;
@@ -39,6 +39,7 @@ struct Layout {
 };
 
 constexpr int NPART = 2 * 304 + 8;
+constexpr int KSMAX = 80;   // most split-K slices of one tensor-core contraction
 constexpr int NSCAL = 64;
 // scalar slots
 constexpr int SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
@@ -53,10 +54,15 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.ldX = rup(X, 8);
     L.ldo2 = rup((long long)o * o, 8);
     L.ldvv = rup((long long)v * v, 8);
-    int rc = op.r_chunk > 0 ? op.r_chunk : 128;
-    if (rc > 256) rc = 256;
-    if (rc > R) rc = R;
-    if (tc && rc % 16) rc = (int)rup(rc, 16) > 256 ? 256 : (int)rup(rc, 16);
+    // r-chunk: at most 256 columns (one N tile), chunks of equal size
+    int rc;
+    if (op.r_chunk > 0) {
+        rc = op.r_chunk > 256 ? 256 : op.r_chunk;
+    } else {
+        const int nch = (R + 255) / 256;
+        rc = (R + nch - 1) / nch;
+    }
+    if (tc) rc = (int)rup(rc, 16) > 256 ? 256 : (int)rup(rc, 16);
     if (rc > R) rc = R;
     L.rc = rc;
     const long long dim = v > o ? v : o;
@@ -95,6 +101,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     const size_t none = (size_t)-1;
     L.T64 = L.W64 = L.Y64 = L.S64 = none;
     L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
+    L.PART = none;
     if (!tc) {
         L.T64 = take((size_t)R * v * v * d);
         L.W64 = take((size_t)rc * X * v * d);
@@ -116,6 +123,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.WTa = take((size_t)rc * v * L.ldX * e);
         L.WTb = take((size_t)rc * v * L.ldX * e);
         L.S = take((size_t)rc * L.ldvv * e);
+        L.PART = take((size_t)KSMAX * (size_t)(v > o * o ? v : o * o) * rc * sizeof(float));
     }
     L.total = off;
     return true;
@@ -215,7 +223,8 @@ int auto_ksplit(int M, int N, int bn, int K, int prec) {
     const int ke = prec == PPL_PREC_BF16X3 ? 64 : 32;
     const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
     const long long nkb = (K + ke - 1) / ke;
-    long long ks = (304 + tiles - 1) / tiles;
+    long long ks = (152 + tiles - 1) / tiles;
+    if (ks > KSMAX) ks = KSMAX;
     if (ks > nkb) ks = nkb;
     if (ks < 1) ks = 1;
     return (int)ks;
@@ -385,10 +394,33 @@ int t_tc(ppl_cpd* h) {
     g.out = out_split(opb(h, h->L.T), pT, 0, v, ldv, 1, 0, 0, (long long)v * ldv);
     int rc = run_tc(h, g, "T");
     if (rc) return rc;
-    // T transposed: Tt[r][d][c] = T[r][c][d], produced by a second epilogue pass of the same GEMM
-    TcGemm gt = g;
-    gt.out = out_split(opb(h, h->L.Tt), pT, 0, v, 1, ldv, 0, 0, (long long)v * ldv);
-    return run_tc(h, gt, "Tt");
+    // T transposed per r: Tt[r][d][c] = T[r][c][d]
+    transpose_operand(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, v, ldv, (long long)v * ldv, R, h->st);
+    return PPL_OK;
+}
+
+// split-K contraction through FP32 partials [ks][n][m] in L.PART, then an FP64
+// reduction into out[m * ldo + n]
+int run_tc_partial(ppl_cpd* h, TcGemm& g, double* out, long long ldo, const char* what) {
+    g.prec = h->opts.precision;
+    if (g.bn == 0) g.bn = bn_for(g.N);
+    g.ksplit = auto_ksplit(g.M, g.N, g.bn, g.K, g.prec);
+    const int ke = g.prec == PPL_PREC_BF16X3 ? 64 : 32;
+    const int nkb = (g.K + ke - 1) / ke;
+    const int per = (nkb + g.ksplit - 1) / g.ksplit;
+    const int ks = (nkb + per - 1) / per;      // the split count the kernel will use
+    float* part = h->at<float>(h->L.PART);
+    g.out = TcOut{};
+    g.out.kind = EPI_F32;
+    g.out.out = part;
+    g.out.sk = (long long)g.M * g.N;
+    g.out.sm_lo = 1;
+    g.out.sn_lo = g.M;
+    g.out.alpha = 1.0f;
+    int e = run_tc(h, g, what);
+    if (e) return e;
+    reduce_partials(part, ks, g.M, g.N, out, ldo, h->st);
+    return PPL_OK;
 }
 
 int chain_tc(ppl_cpd* h, int mode, double* Mout) {
@@ -398,7 +430,6 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
     const long long pU = (long long)R * ldv;
     const long long pT = (long long)R * v * ldv;
     const long long pW = (long long)rc * X * ldv;
-    cudaMemsetAsync(Mout, 0, (size_t)v * R * sizeof(double), h->st);
     uop(h, mode == 0 ? 1 : 0, h->L.UopA);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
@@ -425,11 +456,7 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
         g3.A = mat(opb(h, h->L.Bp), pB, v, (int)(X * ldv), 1, X * ldv, 0);
         g3.B = mat(opb(h, h->L.Y), pW, rc, (int)(X * ldv), 1, X * ldv, 0);
         g3.M = v; g3.N = rcur; g3.K = (int)(X * ldv); g3.batch = 1;
-        g3.bn = bn_for(rcur);
-        g3.ksplit = auto_ksplit(v, rcur, g3.bn, g3.K, h->opts.precision);
-        g3.out = TcOut{};
-        g3.out.kind = EPI_ATOMIC_F64; g3.out.out = Mout + r0; g3.out.sm_lo = R; g3.out.sn_lo = 1; g3.out.alpha = 1.0f;
-        e = run_tc(h, g3, "M");
+        e = run_tc_partial(h, g3, Mout + r0, R, "M");
         if (e) return e;
     }
     return PPL_OK;
@@ -443,7 +470,6 @@ int p_tc(ppl_cpd* h) {
     const long long pWT = (long long)rc * v * ldX;
     const long long pS = (long long)rc * ldvv;
     double* P = h->at<double>(h->L.P);
-    cudaMemsetAsync(P, 0, (size_t)o * o * R * sizeof(double), h->st);
     uop(h, 0, h->L.UopA);
     uop(h, 1, h->L.UopB);
     for (int r0 = 0; r0 < R; r0 += rc) {
@@ -472,11 +498,7 @@ int p_tc(ppl_cpd* h) {
         gp.A = mat(opb(h, h->L.tauN), (long long)o * o * ldvv, o * o, v * v, 1, ldvv, 0);
         gp.B = mat(opb(h, h->L.S), pS, rc, v * v, 1, ldvv, 0);
         gp.M = o * o; gp.N = rcur; gp.K = v * v; gp.batch = 1;
-        gp.bn = bn_for(rcur);
-        gp.ksplit = auto_ksplit(o * o, rcur, gp.bn, gp.K, h->opts.precision);
-        gp.out = TcOut{};
-        gp.out.kind = EPI_ATOMIC_F64; gp.out.out = P + r0; gp.out.sm_lo = R; gp.out.sn_lo = 1; gp.out.alpha = 1.0f;
-        e = run_tc(h, gp, "P");
+        e = run_tc_partial(h, gp, P + r0, R, "P");
         if (e) return e;
     }
     return PPL_OK;

@@ -79,7 +79,8 @@ enum TcEpi { EPI_SPLIT = 0, EPI_F32 = 1, EPI_ATOMIC_F64 = 2, EPI_ATOMIC_F32 = 3 
 struct TcOut {
     int kind;               // TcEpi; EPI_SPLIT writes operand planes of the same precision
     void* out; long long plane_elems;
-    long long sb, sm_hi, sm_lo, sn_hi, sn_lo;
+    long long sb, sk;       // batch stride; split-K slice stride (EPI_F32 partials)
+    long long sm_hi, sm_lo, sn_hi, sn_lo;
     int mdiv, ndiv;
     float alpha;
 };
@@ -95,6 +96,11 @@ struct TcGemm {
     TcOut out;
 };
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);
+// out[m * ldo + n] = sum_k part[k][n][m] (FP64 sum of FP32 split-K partials, deterministic)
+void reduce_partials(const float* part, int ksplit, int M, int N, double* out, long long ldo, cudaStream_t s);
+// dst[b][j][i] = src[b][i][j], i, j < n, operand planes of the given precision
+void transpose_operand(int prec, const void* src, void* dst, long long plane_elems, int n, long long ld,
+                       long long bstride, int batch, cudaStream_t s);
 int tc_init_driver();   // resolves cuTensorMapEncodeTiled; returns 0 on success
 // FP64 -> operand planes: dst[b][r][c] from src with generic index maps, rows x cols per batch
 struct SplitSrc {

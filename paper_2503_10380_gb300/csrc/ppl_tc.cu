@@ -36,12 +36,12 @@ constexpr unsigned long long WAIT_NS = 500ull * 1000ull * 1000ull;   // 0.5 s pe
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 struct KParams {
-    int M, N, K, bn, ksplit, nkb_total, per_split, stages;
+    int M, N, K, bn, acc_cols, ksplit, nkb_total, per_split, stages;
     int a_row0, b_row0, a_b0, b_b0, a_bstep, b_bstep;
     int batch;
     int kind;
     void* out;
-    long long plane, sb, sm_hi, sm_lo, sn_hi, sn_lo;
+    long long plane, sb, sk, sm_hi, sm_lo, sn_hi, sn_lo;
     int mdiv, ndiv;
     float alpha;
     unsigned int* err;
@@ -147,7 +147,7 @@ __device__ __forceinline__ float round_tf32(float x) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
     constexpr bool SPLIT = (PREC == PPL_PREC_BF16X3);
@@ -155,14 +155,11 @@ __global__ void __launch_bounds__(128, 1)
     constexpr int KSTEP = SPLIT ? 16 : 8;     // K per MMA instruction
     constexpr int ASTEP_BYTES = KSTEP * (SPLIT ? 2 : 4);   // 32 bytes
 
-    const int bz = blockIdx.z / p.ksplit, ks = blockIdx.z % p.ksplit;
-    const int kb0 = ks * p.per_split;
-    int nk = p.nkb_total - kb0;
-    if (nk > p.per_split) nk = p.per_split;
-    if (nk <= 0) return;   // empty split-K slice: nothing to add
-
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * p.bn;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn;
+    const int tiles_mn = ntm * ntn;
+    const int total = tiles_mn * p.batch * p.ksplit;
+    const int S = p.stages;
 
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -172,24 +169,33 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t a_bytes = TM * KROW_BYTES;
     const uint32_t b_bytes = (uint32_t)p.bn * KROW_BYTES;
     const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (a_bytes + b_bytes);
-    const uint32_t bar_off = stage_bytes * p.stages;
-    const uint32_t full0 = base + bar_off;                 // stages x 8 bytes
-    const uint32_t empty0 = full0 + 8u * p.stages;
-    const uint32_t done_bar = empty0 + 8u * p.stages;
-    const uint32_t slot = done_bar + 8u;                   // TMEM address slot
-    volatile uint32_t* slot_ptr = (volatile uint32_t*)(gbase + bar_off + 16u * p.stages + 8u);
+    const uint32_t bar_off = stage_bytes * S;
+    const uint32_t full0 = base + bar_off;
+    const uint32_t empty0 = full0 + 8u * S;
+    const uint32_t tfull0 = empty0 + 8u * S;     // 2 accumulators
+    const uint32_t tempty0 = tfull0 + 16u;
+    const uint32_t drain_bar = tempty0 + 16u;
+    const uint32_t slot = drain_bar + 8u;
+    volatile uint32_t* slot_ptr = (volatile uint32_t*)(gbase + (slot - base));
     __shared__ int s_fail;
+    __shared__ int s_issued, s_consumed;
 
-    uint32_t ncols = 32;
-    while ((int)ncols < p.bn) ncols <<= 1;
+    const uint32_t acc_cols = (uint32_t)p.acc_cols;
+    const uint32_t ncols = 2u * acc_cols;
 
     if (threadIdx.x == 0) {
         s_fail = 0;
-        for (int s = 0; s < p.stages; ++s) {
+        s_issued = 0;
+        s_consumed = 0;
+        for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8u * s, 1);
             mbar_init(empty0 + 8u * s, 1);
         }
-        mbar_init(done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8u * b, 1);
+            mbar_init(tempty0 + 8u * b, 4);
+        }
+        mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mAh) : "memory");
@@ -204,118 +210,159 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *slot_ptr;
+    volatile int* vfail = &s_fail;
 
-    int issued = 0, consumed = 0;
-    const int a_b = p.a_b0 + bz * p.a_bstep;
-    const int b_b = p.b_b0 + bz * p.b_bstep;
-
-    if (warp == 0 && lane == 0) {
-        // producer
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % p.stages;
-            if (it >= p.stages) {
-                if (!mbar_wait(empty0 + 8u * s, (uint32_t)((it / p.stages - 1) & 1))) {
-                    atomicOr(p.err, 1u);
-                    s_fail = 1;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: one ring of S stages shared by all tiles of this block
+            int it = 0;
+            for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
+                const int z = t / tiles_mn, rem = t % tiles_mn;
+                const int m0 = (rem % ntm) * TM, n0 = (rem / ntm) * p.bn;
+                const int bz = z / p.ksplit, ks = z % p.ksplit;
+                const int kb0 = ks * p.per_split;
+                const int nk = min(p.per_split, p.nkb_total - kb0);
+                const int a_b = p.a_b0 + bz * p.a_bstep, b_b = p.b_b0 + bz * p.b_bstep;
+                for (int kbi = 0; kbi < nk; ++kbi, ++it) {
+                    const int s = it % S;
+                    if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1))) {
+                        atomicOr(p.err, 1u);
+                        *vfail = 1;
+                        break;
+                    }
+                    const uint32_t sa = base + stage_bytes * s;
+                    const uint32_t fb = full0 + 8u * s;
+                    mbar_expect_tx(fb, stage_bytes);
+                    const int kc = (kb0 + kbi) * KE;
+                    tma_load_3d(sa, &mAh, kc, p.a_row0 + m0, a_b, fb);
+                    tma_load_3d(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, kc, p.b_row0 + n0, b_b, fb);
+                    if constexpr (SPLIT) {
+                        tma_load_3d(sa + a_bytes, &mAl, kc, p.a_row0 + m0, a_b, fb);
+                        tma_load_3d(sa + 2u * a_bytes + b_bytes, &mBl, kc, p.b_row0 + n0, b_b, fb);
+                    }
+                    s_issued = it + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
+            idesc |= SPLIT ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+            int it = 0, li = 0;
+            for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
+                const int z = t / tiles_mn;
+                const int ks = z % p.ksplit;
+                const int kb0 = ks * p.per_split;
+                const int nk = min(p.per_split, p.nkb_total - kb0);
+                const int buf = li & 1;
+                if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
+                    atomicOr(p.err, 8u);
+                    *vfail = 1;
                     break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)buf * acc_cols;
+                bool ok = true;
+                for (int kbi = 0; kbi < nk; ++kbi, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
+                        atomicOr(p.err, 2u);
+                        *vfail = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + stage_bytes * s;
+                    const uint32_t sah = sa, sal = sa + a_bytes;
+                    const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+                    const int kc = (kb0 + kbi) * KE;
+                    int ksteps = KE / KSTEP;
+                    if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+                    const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+                    const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                        mma<PREC>(d, dah + off, dbh + off, idesc, (kbi > 0 || kk > 0) ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            mma<PREC>(d, dah + off, dbl + off, idesc, 1u);
+                            mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                        }
+                    }
+                    mma_commit(empty0 + 8u * s);
+                    s_consumed = it + 1;
+                }
+                if (!ok) break;
+                mma_commit(tfull0 + 8u * buf);
+                ++li;
             }
-            if (*(volatile int*)&s_fail) break;
-            const uint32_t sa = base + stage_bytes * s;
-            const uint32_t fb = full0 + 8u * s;
-            mbar_expect_tx(fb, stage_bytes);
-            const int kc = (kb0 + it) * KE;
-            tma_load_3d(sa, &mAh, kc, p.a_row0 + m0, a_b, fb);
-            tma_load_3d(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, kc, p.b_row0 + n0, b_b, fb);
-            if constexpr (SPLIT) {
-                tma_load_3d(sa + a_bytes, &mAl, kc, p.a_row0 + m0, a_b, fb);
-                tma_load_3d(sa + 2u * a_bytes + b_bytes, &mBl, kc, p.b_row0 + n0, b_b, fb);
-            }
-            issued = it + 1;
+            mma_commit(drain_bar);   // completes once every MMA issued here has finished
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
-        idesc |= SPLIT ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % p.stages;
-            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / p.stages) & 1))) {
-                atomicOr(p.err, 2u);
-                s_fail = 1;
+    } else {
+        // epilogue: warps 2..5 read TMEM lanes 32*(warp%4) .. +31
+        const int q = warp & 3;
+        int li = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int z = t / tiles_mn, rem = t % tiles_mn;
+            const int m0 = (rem % ntm) * TM, n0 = (rem / ntm) * p.bn;
+            const int bz = z / p.ksplit, ks = z % p.ksplit;
+            const int buf = li & 1;
+            if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
+                if (lane == 0) atomicOr(p.err, 4u);
+                *vfail = 1;
                 break;
             }
+            if (*vfail) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = base + stage_bytes * s;
-            const uint32_t sah = sa, sal = sa + a_bytes;
-            const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
-            const int kc = (kb0 + it) * KE;
-            int ksteps = KE / KSTEP;
-            if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
-            const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
-            const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
-            for (int kk = 0; kk < ksteps; ++kk) {
-                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                mma<PREC>(tmem, dah + off, dbh + off, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-                if constexpr (SPLIT) {
-                    mma<PREC>(tmem, dah + off, dbl + off, idesc, 1u);
-                    mma<PREC>(tmem, dal + off, dbh + off, idesc, 1u);
-                }
-            }
-            mma_commit(empty0 + 8u * s);
-            consumed = it + 1;
-        }
-        mma_commit(done_bar);
-    }
-    __syncwarp();
-
-    // epilogue: wait for the accumulator
-    bool ok = mbar_wait(done_bar, 0);
-    if (!ok) {
-        if (lane == 0) atomicOr(p.err, 4u);
-        s_fail = 1;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    const bool failed = (*(volatile int*)&s_fail) != 0;
-
-    if (!failed) {
-        const int m = m0 + warp * 32 + lane;
-        const bool mrow = (m < p.M);
-        long long mo = 0;
-        if (mrow) mo = (long long)bz * p.sb + (long long)(m / p.mdiv) * p.sm_hi + (long long)(m % p.mdiv) * p.sm_lo;
-        for (int c0 = 0; c0 < p.bn; c0 += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (!mrow) continue;
+            const int m = m0 + q * 32 + lane;
+            const bool mrow = (m < p.M);
+            long long mo = 0;
+            if (mrow)
+                mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(m / p.mdiv) * p.sm_hi +
+                     (long long)(m % p.mdiv) * p.sm_lo;
+            const uint32_t tb = tmem + (uint32_t)buf * acc_cols + ((uint32_t)(q * 32) << 16);
+            for (int c0 = 0; c0 < p.bn; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tb + (uint32_t)c0, v);
+                if (!mrow) continue;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c0 + j;
-                if (n >= p.N) break;
-                const long long idx = mo + (long long)(n / p.ndiv) * p.sn_hi + (long long)(n % p.ndiv) * p.sn_lo;
-                const float x = p.alpha * __uint_as_float(v[j]);
-                if (p.kind == EPI_SPLIT) {
-                    if constexpr (SPLIT) {
-                        __nv_bfloat16* o = (__nv_bfloat16*)p.out;
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                        o[idx] = hi;
-                        o[idx + p.plane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= p.N) break;
+                    const long long idx = mo + (long long)(n / p.ndiv) * p.sn_hi + (long long)(n % p.ndiv) * p.sn_lo;
+                    const float x = p.alpha * __uint_as_float(v[j]);
+                    if (p.kind == EPI_SPLIT) {
+                        if constexpr (SPLIT) {
+                            __nv_bfloat16* o = (__nv_bfloat16*)p.out;
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                            o[idx] = hi;
+                            o[idx + p.plane] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                        } else {
+                            ((float*)p.out)[idx] = round_tf32(x);
+                        }
+                    } else if (p.kind == EPI_F32) {
+                        ((float*)p.out)[idx] = x;
+                    } else if (p.kind == EPI_ATOMIC_F64) {
+                        atomicAdd((double*)p.out + idx, (double)x);
                     } else {
-                        ((float*)p.out)[idx] = round_tf32(x);
+                        atomicAdd((float*)p.out + idx, x);
                     }
-                } else if (p.kind == EPI_F32) {
-                    ((float*)p.out)[idx] = x;
-                } else if (p.kind == EPI_ATOMIC_F64) {
-                    atomicAdd((double*)p.out + idx, (double)x);
-                } else {
-                    atomicAdd((float*)p.out + idx, x);
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
+            ++li;
         }
-    } else if (threadIdx.x == 0) {
-        // drain TMA writes that were issued but never consumed
-        for (int it = consumed; it < issued; ++it) {
-            const int s = it % p.stages;
-            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / p.stages) & 1))) break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // every MMA of this block has completed before TMEM is released
+        if (!mbar_wait(drain_bar, 0)) atomicOr(p.err, 32u);
+        if (*vfail) {
+            // loads issued but never consumed must land before the block exits
+            for (int it = s_consumed; it < s_issued; ++it)
+                if (!mbar_wait(full0 + 8u * (it % S), (uint32_t)((it / S) & 1))) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -323,6 +370,42 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 2) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// Sum split-K partials part[ks][n][m] (fp32) in FP64 into out[m * ldo + n].
+__global__ void k_reduce_partials(const float* part, int ksplit, int M, int N, double* out, long long ldo) {
+    const long long total = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e % M), n = (int)(e / M);
+        double s = 0.0;
+        for (int k = 0; k < ksplit; ++k) s += (double)part[(long long)k * total + e];
+        out[(long long)m * ldo + n] = s;
+    }
+}
+
+// Batched transpose of operand planes: dst[b][j][i] = src[b][i][j] for i, j < n
+// (row stride ld); 2-byte elements in two planes (BF16X3) or 4-byte in one (TF32).
+template <typename T, int PLANES>
+__global__ void k_transpose(const T* src, T* dst, long long plane, int n, long long ld, long long bstride) {
+    __shared__ T tile[PLANES][32][33];
+    const int tiles = (n + 31) / 32;
+    const int b = blockIdx.z;
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (ti >= tiles || tj >= tiles) return;
+    const int i0 = ti * 32, j0 = tj * 32;
+    const long long off = (long long)b * bstride;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, j = j0 + threadIdx.x;
+        for (int pl = 0; pl < PLANES; ++pl)
+            tile[pl][r][threadIdx.x] = (i < n && j < n) ? src[pl * plane + off + (long long)i * ld + j] : T(0);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        if (i < n && j < n)
+            for (int pl = 0; pl < PLANES; ++pl) dst[pl * plane + off + (long long)j * ld + i] = tile[pl][threadIdx.x][r];
     }
 }
 
@@ -420,16 +503,26 @@ int tc_init_driver() {
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0 || g.K <= 0) return 0;
     if (tc_init_driver() != 0) return -1;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) return -7;
+    }
     const bool split = (g.prec == PPL_PREC_BF16X3);
     const int KE = split ? 64 : 32;
     KParams p{};
     p.M = g.M; p.N = g.N; p.K = g.K;
     p.bn = g.bn > 0 ? g.bn : choose_bn(g.N);
+    if (p.bn % 16 || p.bn > 256) return -8;
+    p.acc_cols = 32;
+    while (p.acc_cols < p.bn) p.acc_cols <<= 1;
     p.nkb_total = (g.K + KE - 1) / KE;
     p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
     if (p.ksplit > p.nkb_total) p.ksplit = p.nkb_total;
     p.per_split = (p.nkb_total + p.ksplit - 1) / p.ksplit;
-    p.ksplit = (p.nkb_total + p.per_split - 1) / p.per_split;
+    p.ksplit = (p.nkb_total + p.per_split - 1) / p.per_split;   // every split slice is non-empty
     const int stage_bytes = (split ? 2 : 1) * (TM + p.bn) * KROW_BYTES;
     p.stages = SMEM_BUDGET / stage_bytes;
     if (p.stages > 8) p.stages = 8;
@@ -438,7 +531,8 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.a_bstep = g.a_bstep; p.b_bstep = g.b_bstep;
     p.batch = g.batch;
     p.kind = g.out.kind; p.out = g.out.out; p.plane = g.out.plane_elems;
-    p.sb = g.out.sb; p.sm_hi = g.out.sm_hi; p.sm_lo = g.out.sm_lo; p.sn_hi = g.out.sn_hi; p.sn_lo = g.out.sn_lo;
+    p.sb = g.out.sb; p.sk = g.out.sk;
+    p.sm_hi = g.out.sm_hi; p.sm_lo = g.out.sm_lo; p.sn_hi = g.out.sn_hi; p.sn_lo = g.out.sn_lo;
     p.mdiv = g.out.mdiv > 0 ? g.out.mdiv : (1 << 30);
     p.ndiv = g.out.ndiv > 0 ? g.out.ndiv : (1 << 30);
     p.alpha = g.out.alpha;
@@ -457,14 +551,33 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     }
     const size_t smem = (size_t)stage_bytes * p.stages + 1024 + 16 * p.stages + 64;
     if (smem > (size_t)SMEM_ATTR) return -6;
-    dim3 grid((g.M + TM - 1) / TM, (g.N + p.bn - 1) / p.bn, g.batch * p.ksplit);
-    if (grid.y > 65535 || grid.z > 65535) return -4;
+    const long long tiles = (long long)((g.M + TM - 1) / TM) * ((g.N + p.bn - 1) / p.bn) * g.batch * p.ksplit;
+    if (tiles > (1ll << 30)) return -4;
+    const int grid = (int)(tiles < sms ? tiles : sms);
     if (split)
-        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
+        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 192, smem, s>>>(mAh, mAl, mBh, mBl, p);
     else
-        k_tc_gemm<PPL_PREC_TF32><<<grid, 128, smem, s>>>(mAh, mAl, mBh, mBl, p);
+        k_tc_gemm<PPL_PREC_TF32><<<grid, 192, smem, s>>>(mAh, mAl, mBh, mBl, p);
     const cudaError_t le = cudaGetLastError();
     return le == cudaSuccess ? 0 : -(1000 + (int)le);
+}
+
+void reduce_partials(const float* part, int ksplit, int M, int N, double* out, long long ldo, cudaStream_t s) {
+    const long long total = (long long)M * N;
+    if (total <= 0) return;
+    k_reduce_partials<<<grid_for(total, 256), 256, 0, s>>>(part, ksplit, M, N, out, ldo);
+}
+
+void transpose_operand(int prec, const void* src, void* dst, long long plane_elems, int n, long long ld,
+                       long long bstride, int batch, cudaStream_t s) {
+    if (n <= 0 || batch <= 0) return;
+    const int tiles = (n + 31) / 32;
+    dim3 grid(tiles, tiles, batch), block(32, 8);
+    if (prec == PPL_PREC_BF16X3)
+        k_transpose<unsigned short, 2><<<grid, block, 0, s>>>((const unsigned short*)src, (unsigned short*)dst,
+                                                              plane_elems, n, ld, bstride);
+    else
+        k_transpose<float, 1><<<grid, block, 0, s>>>((const float*)src, (float*)dst, plane_elems, n, ld, bstride);
 }
 
 void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch, void* dst, long long plane_elems,
