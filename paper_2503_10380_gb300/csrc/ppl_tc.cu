@@ -9,9 +9,11 @@
 //           Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial
 //           intelligence datatype for higher-precision computations" (2019);
 //   TF32:   operands rounded to tf32 (round to nearest) when written, one MMA.
-// One CTA of 128 threads computes one 128 x bn tile: lane 0 of warp 0 issues
-// TMA, lane 0 of warp 1 issues MMAs, warp 2 owns the TMEM allocation, and all
-// four warps run the epilogue (warp w reads TMEM lanes 32w..32w+31).
+// Persistent: one CTA per SM walks the 128 x bn output tiles.  Lane 0 of warp
+// 0 issues TMA into a ring of shared-memory stages, lane 0 of warp 1 issues the
+// MMAs into one of two TMEM accumulators, and warps 2..9 drain the other
+// accumulator to global memory, so a tile's epilogue overlaps the next tile's
+// mainloop.  Warp 2 owns the TMEM allocation.
 // Every mbarrier wait is bounded; on expiry the kernel records the error,
 // drains what it issued, frees TMEM and returns.
 #include "ppl_internal.h"
@@ -130,14 +132,18 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
 }
 
 __device__ __forceinline__ float round_tf32(float x) {
@@ -147,7 +153,7 @@ __device__ __forceinline__ float round_tf32(float x) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
     constexpr bool SPLIT = (PREC == PPL_PREC_BF16X3);
@@ -155,6 +161,7 @@ __global__ void __launch_bounds__(192, 1)
     constexpr int KSTEP = SPLIT ? 16 : 8;     // K per MMA instruction
     constexpr int ASTEP_BYTES = KSTEP * (SPLIT ? 2 : 4);   // 32 bytes
 
+    constexpr int NEPI = 8;                   // epilogue warps: two per TMEM lane quarter
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn;
     const int tiles_mn = ntm * ntn;
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull0 + 8u * b, 1);
-            mbar_init(tempty0 + 8u * b, 4);
+            mbar_init(tempty0 + 8u * b, NEPI);
         }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -299,8 +306,9 @@ __global__ void __launch_bounds__(192, 1)
             mma_commit(drain_bar);   // completes once every MMA issued here has finished
         }
     } else {
-        // epilogue: warps 2..5 read TMEM lanes 32*(warp%4) .. +31
-        const int q = warp & 3;
+        // epilogue: warps 2..9; warp w reads TMEM lanes 32*(w%4) .. +31 and every
+        // other 32-column chunk of the accumulator
+        const int q = warp & 3, half = (warp - 2) >> 2;
         int li = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             const int z = t / tiles_mn, rem = t % tiles_mn;
@@ -321,32 +329,42 @@ __global__ void __launch_bounds__(192, 1)
                 mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(m / p.mdiv) * p.sm_hi +
                      (long long)(m % p.mdiv) * p.sm_lo;
             const uint32_t tb = tmem + (uint32_t)buf * acc_cols + ((uint32_t)(q * 32) << 16);
-            for (int c0 = 0; c0 < p.bn; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tb + (uint32_t)c0, v);
-                if (!mrow) continue;
+            const long long sn = p.sn_lo;
+            for (int c0 = half * 32; c0 < p.bn; c0 += 64) {
+                uint32_t v[32];
+                tmem_ld32(tb + (uint32_t)c0, v);
+                const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));   // this tile's columns only
+                if (!mrow || nvalid <= 0) continue;
+                long long idx = mo + (long long)(n0 + c0) * sn;
+                if (p.kind == EPI_SPLIT) {
+                    if constexpr (SPLIT) {
+                        __nv_bfloat16* o = (__nv_bfloat16*)p.out + idx;
+                        __nv_bfloat16* ol = o + p.plane;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n >= p.N) break;
-                    const long long idx = mo + (long long)(n / p.ndiv) * p.sn_hi + (long long)(n % p.ndiv) * p.sn_lo;
-                    const float x = p.alpha * __uint_as_float(v[j]);
-                    if (p.kind == EPI_SPLIT) {
-                        if constexpr (SPLIT) {
-                            __nv_bfloat16* o = (__nv_bfloat16*)p.out;
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                            o[idx] = hi;
-                            o[idx + p.plane] = __float2bfloat16_rn(x - __bfloat162float(hi));
-                        } else {
-                            ((float*)p.out)[idx] = round_tf32(x);
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < nvalid) {
+                                const float x = __uint_as_float(v[j]);
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                                o[j * sn] = hi;
+                                ol[j * sn] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                            }
                         }
-                    } else if (p.kind == EPI_F32) {
-                        ((float*)p.out)[idx] = x;
-                    } else if (p.kind == EPI_ATOMIC_F64) {
-                        atomicAdd((double*)p.out + idx, (double)x);
                     } else {
-                        atomicAdd((float*)p.out + idx, x);
+                        float* o = (float*)p.out + idx;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < nvalid) o[j * sn] = round_tf32(__uint_as_float(v[j]));
                     }
+                } else if (p.kind == EPI_F32) {
+                    float* o = (float*)p.out + idx;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j < nvalid) o[j * sn] = __uint_as_float(v[j]);
+                } else {
+                    double* o = (double*)p.out + idx;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j < nvalid) atomicAdd(o + j * sn, (double)__uint_as_float(v[j]));
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -534,8 +552,9 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.sb = g.out.sb; p.sk = g.out.sk;
     p.sm_hi = g.out.sm_hi; p.sm_lo = g.out.sm_lo; p.sn_hi = g.out.sn_hi; p.sn_lo = g.out.sn_lo;
     p.mdiv = g.out.mdiv > 0 ? g.out.mdiv : (1 << 30);
-    p.ndiv = g.out.ndiv > 0 ? g.out.ndiv : (1 << 30);
-    p.alpha = g.out.alpha;
+    p.ndiv = 1 << 30;
+    if (g.out.ndiv > 0 || g.out.sn_hi != 0 || g.out.alpha != 1.0f) return -9;   // columns map by one stride
+    p.alpha = 1.0f;
     p.err = err_flag;
 
     CUtensorMap mAh, mAl, mBh, mBl;
@@ -555,9 +574,9 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (tiles > (1ll << 30)) return -4;
     const int grid = (int)(tiles < sms ? tiles : sms);
     if (split)
-        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 192, smem, s>>>(mAh, mAl, mBh, mBl, p);
+        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 320, smem, s>>>(mAh, mAl, mBh, mBl, p);
     else
-        k_tc_gemm<PPL_PREC_TF32><<<grid, 192, smem, s>>>(mAh, mAl, mBh, mBl, p);
+        k_tc_gemm<PPL_PREC_TF32><<<grid, 320, smem, s>>>(mAh, mAl, mBh, mBl, p);
     const cudaError_t le = cudaGetLastError();
     return le == cudaSuccess ? 0 : -(1000 + (int)le);
 }
