@@ -98,11 +98,21 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
 
 // Factor the kb x kb diagonal block held in Ls (lower) in place, clamping
 // pivots at tol, and form its inverse in Li (lower).  All NT threads.
-// Right-looking on unscaled columns: with d_j the (clamped) pivot,
-// A[i][c] -= A[i][j] A[c][j] / d_j, so a column costs one division; the
-// square roots and column scalings are applied in one parallel pass at the end.
-__device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* rd, int kb, double tol,
-                            unsigned long long* nclamp) {
+//
+// GB300 issues an FP64 warp instruction at the same cost whether or not its
+// lanes are masked, so both parts keep the FP64 instruction count close to
+// the useful work:
+//  * factorisation: right-looking on unscaled columns (with d_j the clamped
+//    pivot, A[i][c] -= A[i][j] A[c][j] / d_j, one division per column); at step
+//    j only the n(n+1)/2 active elements of the trailing triangle are
+//    enumerated, packed onto consecutive threads through the (row, col) table
+//    tri; square roots and column scalings follow in one parallel pass;
+//  * inverse: 8 x 8 blocks; the four diagonal blocks are inverted by forward
+//    substitution (one warp each), then the off-diagonal blocks block-diagonal
+//    by block-diagonal, Li[I][J] = -Li[I][I] (sum_{K=J}^{I-1} L[I][K] Li[K][J]).
+constexpr int SB = 8;   // inverse sub-block
+__device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* rd, const unsigned short* tri,
+                            double (*Tw)[NB + 1], int kb, double tol, unsigned long long* nclamp) {
     const int t = threadIdx.x;
     for (int j = 0; j < kb; ++j) {
         if (t == 0) {
@@ -116,10 +126,16 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
         }
         __syncthreads();
         const int n = kb - j - 1;
-        const double r = rd[j];
-        for (int e = t; e < n * n; e += NT) {
-            const int ii = j + 1 + e / n, cc = j + 1 + e % n;
-            if (cc <= ii) Ls[ii][cc] = fma(-Ls[ii][j] * r, Ls[cc][j], Ls[ii][cc]);
+        const int nel = n * (n + 1) / 2;
+        if (t < nel) {
+            const unsigned short ic = tri[t];
+            const int ii = j + 1 + (ic >> 8), cc = j + 1 + (ic & 0xff);
+            Ls[ii][cc] = fma(-(Ls[ii][j] * rd[j]), Ls[cc][j], Ls[ii][cc]);
+        }
+        if (t + NT < nel) {
+            const unsigned short ic = tri[t + NT];
+            const int ii = j + 1 + (ic >> 8), cc = j + 1 + (ic & 0xff);
+            Ls[ii][cc] = fma(-(Ls[ii][j] * rd[j]), Ls[cc][j], Ls[ii][cc]);
         }
         __syncthreads();
     }
@@ -130,25 +146,63 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
         Ls[t][t] = sd;
     }
     __syncthreads();
-    for (int e = t; e < kb * kb; e += NT) {
-        const int i = e / kb, j = e % kb;
-        if (j < i) Ls[i][j] *= rd[j];
+    {
+        const int nl = kb * (kb - 1) / 2;    // strictly lower elements, row-major
+        for (int e = t; e < nl; e += NT) {
+            const unsigned short ic = tri[e];
+            const int i = (ic >> 8) + 1, j = ic & 0xff;   // (i, j) with j < i
+            Ls[i][j] *= rd[j];
+        }
     }
     for (int e = t; e < NB * (NB + 1); e += NT) (&Li[0][0])[e] = 0.0;
     __syncthreads();
-    // inverse, column c by 8 threads: Li[i][c] = -(sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
-    const int c = t / 8, q = t % 8;
-    if (c < kb && q == 0) Li[c][c] = rd[c];
-    __syncthreads();
-    for (int i = 1; i < kb; ++i) {
-        double s = 0.0;
-        if (c < i) {
-            for (int k = c + q; k < i; k += 8) s = fma(Ls[i][k], Li[k][c], s);
+    // diagonal 8 x 8 blocks: warp w < 4 inverts block w, lane l < 8 owns column l
+    const int w = t / 32, l = t % 32;
+    if (w < NB / SB && l < SB) {
+        const int o = w * SB, c = o + l;
+        if (c < kb) {
+            double x[SB];
+#pragma unroll
+            for (int i = 0; i < SB; ++i) x[i] = 0.0;
+#pragma unroll
+            for (int i = 0; i < SB; ++i) {
+                if (i >= l && o + i < kb) {
+                    double sacc = (i == l) ? 1.0 : 0.0;
+#pragma unroll
+                    for (int k = 0; k < SB; ++k)
+                        if (k >= l && k < i) sacc = fma(-Ls[o + i][o + k], x[k], sacc);
+                    x[i] = sacc * rd[o + i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < SB; ++i)
+                if (o + i < kb) Li[o + i][c] = x[i];
         }
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if (c < i && q == 0) Li[i][c] = -s * rd[i];
+    }
+    __syncthreads();
+    // off-diagonal blocks, distance dd = I - J
+    const int nblk = (kb + SB - 1) / SB;
+    for (int dd = 1; dd < nblk; ++dd) {
+        const int npair = nblk - dd;
+        // Tw[I-block rows][J-block cols] = sum_{K=J}^{I-1} L[I][K] Li[K][J]
+        for (int e = t; e < npair * SB * SB; e += NT) {
+            const int pr = e / (SB * SB), r = (e / SB) % SB, cl = e % SB;
+            const int J = pr, I = pr + dd;
+            double acc = 0.0;
+            for (int K = J; K < I; ++K)
+#pragma unroll
+                for (int k = 0; k < SB; ++k) acc = fma(Ls[I * SB + r][K * SB + k], Li[K * SB + k][J * SB + cl], acc);
+            Tw[I * SB + r][J * SB + cl] = acc;
+        }
+        __syncthreads();
+        for (int e = t; e < npair * SB * SB; e += NT) {
+            const int pr = e / (SB * SB), r = (e / SB) % SB, cl = e % SB;
+            const int J = pr, I = pr + dd;
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < SB; ++k) acc = fma(Li[I * SB + r][I * SB + k], Tw[I * SB + k][J * SB + cl], acc);
+            Li[I * SB + r][J * SB + cl] = -acc;
+        }
         __syncthreads();
     }
 }
@@ -156,7 +210,7 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
 // load the lower kb x kb block of V at (k0, k0) into Ls, factor it, write L
 // back to V and L^-1 to Linv[k]
 __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB + 1], double (*Li)[NB + 1],
-                             double* rd) {
+                             double* rd, const unsigned short* tri, double (*Tw)[NB + 1]) {
     const int R = p.R, tid = threadIdx.x;
     const int k0 = k * NB, kb = min(NB, R - k0);
     for (int e = tid; e < NB * NB; e += NT) {
@@ -164,7 +218,7 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
         Ls[i][j] = (i < kb && j <= i) ? __ldcg(p.V + (long long)(k0 + i) * R + k0 + j) : 0.0;
     }
     __syncthreads();
-    diag_factor(Ls, Li, rd, kb, tol, p.nclamp);
+    diag_factor(Ls, Li, rd, tri, Tw, kb, tol, p.nclamp);
     for (int e = tid; e < kb * kb; e += NT) {
         const int i = e / kb, j = e % kb;
         if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
@@ -181,6 +235,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     __shared__ double Tb[NB][NB + 1];
     __shared__ double rd[NB];
     __shared__ double red[NT / 32];
+    __shared__ unsigned short tri[NB * (NB + 1) / 2];   // (row << 8) | col of the lower triangle, row-major
     __shared__ int s_flag;
     __shared__ unsigned int s_gen;
 
@@ -189,6 +244,9 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     const long long gtid = (long long)blockIdx.x * NT + tid;
     const long long gthreads = (long long)gridDim.x * NT;
     if (tid == 0) s_gen = ld_vol(&p.sync[1]);
+    for (int i = 0, e = 0; i < NB; ++i)
+        for (int c = 0; c <= i; ++c, ++e)
+            if (e % NT == tid) tri[e] = (unsigned short)((i << 8) | c);
     __syncthreads();
     unsigned int gen = s_gen;   // meaningful in thread 0 only
     const int kb0 = min(NB, R);
@@ -223,7 +281,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         }
         __threadfence();
         __syncthreads();
-        factor_block(p, 0, tol, Ls, Li, rd);
+        factor_block(p, 0, tol, Ls, Li, rd, tri, Tb);
     }
     if (!gsync(p, gen, &s_flag)) return;
 
@@ -322,7 +380,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 }
             __threadfence();
             __syncthreads();
-            if (tile == 0 && k + 1 < nt) factor_block(p, k + 1, tol, Ls, Li, rd);
+            if (tile == 0 && k + 1 < nt) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
         }
         if (!gsync(p, gen, &s_flag)) return;
     }
