@@ -131,6 +131,12 @@ int ppl_cpd_energy(ppl_cpd* h, double* E_cp);
  * ||R||^2 in the handle for ppl_cpd_fit.  Cost 2 X v^4 + 2 o^2 v^4 flops, FP64. */
 int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_out);
 
+/* The CP model in canonical form, R~[a,b,i,j] = sum_r lam_r Ua[a,r] Ub[b,r] Ui[i,r] Uj[j,r],
+ * written to R_out [v][v][o][o] (FP64, device); with symmetrise != 0 it is
+ * replaced by 0.5 (R~[a,b,i,j] + R~[b,a,j,i]), the post-reconstruction
+ * symmetrisation of the CPD-PPL section.  2 v^2 o^2 R flops, FP64. */
+int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise);
+
 /* Point the handle at a new tau (same shape, device) for the next CC-like
  * step; the factors in the caller's buffer are kept as the warm start
  * (the paper's "Optimal guess", Role of the Initial Guess section).  The
@@ -143,6 +149,30 @@ int ppl_cpd_set_tau(ppl_cpd* h, const double* tau);
  *   ms[5] S and P contractions (modes i, j)    ms[6] solves i and j    ms[7] fit terms
  * ENOTREADY if profiling is off or no sweep has run. */
 int ppl_cpd_phase_ms(ppl_cpd* h, double* ms);
+
+/* ---- stopping rules and initial guesses (Low cost CPD stopping condition and
+ *      Role of the Initial Guess sections) ------------------------------------------- */
+#define PPL_STOP_FIXED 0   /* exactly max_sweeps sweeps                                          */
+#define PPL_STOP_DFIT  1   /* after sweep n >= 2: |fit_n - fit_{n-1}| < eps (Eq. canon); needs ||R||^2 */
+#define PPL_STOP_ETA   2   /* after sweep n >= 1: eta_n < eps (Eq. N3_stopping); needs want_eta    */
+
+#define PPL_GUESS_OPTIMAL      0  /* start each solve from the current factors (default)          */
+#define PPL_GUESS_NEAR_OPTIMAL 1  /* cache the iterate n-5 of a solve that needed n > 5 sweeps and
+                                     start every later solve from the cache                       */
+#define PPL_GUESS_RANDOM       2  /* start every solve from the guess given to ppl_cpd_init       */
+
+/* Choose how ppl_cpd_solve starts its second and later solves.  The first
+ * solve always starts from the factors in the caller's buffer.  While no
+ * Near-Optimal cache exists yet, the guess given to ppl_cpd_init is used. */
+int ppl_cpd_set_guess_policy(ppl_cpd* h, int policy);
+
+/* One CPD: ALS sweeps until stop_rule fires or max_sweeps is reached.
+ * sweeps_done (host, may be NULL) receives n; fit_hist / eta_hist (host,
+ * [max_sweeps] each, may be NULL) the per-sweep fit (NaN if ||R||^2 unknown)
+ * and eta (NaN unless want_eta).  EINVAL for PPL_STOP_ETA without want_eta,
+ * ENOTREADY for PPL_STOP_DFIT without ||R||^2. */
+int ppl_cpd_solve(ppl_cpd* h, int max_sweeps, int stop_rule, double eps, int* sweeps_done,
+                  double* fit_hist, double* eta_hist);
 
 /* The caller has written a new guess into its factor buffer (the layout of
  * ppl_cpd_init): recompute the Gram matrices the solves use and reset lam to 1. */

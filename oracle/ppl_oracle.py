@@ -370,3 +370,57 @@ def exact_contract(B: np.ndarray, tau: np.ndarray, o: int):
     v = B.shape[1] - o
     _, n2, E = exact_rows(B, tau, o, range(v))
     return n2, E
+
+
+# --------------------------------------------------------------------------
+# stopping rules and initial-guess policies
+# --------------------------------------------------------------------------
+
+def cp_solve(Bvv, tau, U0: dict, max_sweeps: int, rule: str = "fixed", eps: float = 0.0,
+             normR2: float | None = None, lam0=None):
+    """ALS sweeps until a stopping rule fires (Low cost CPD stopping condition section).
+
+    rule "fixed": exactly max_sweeps sweeps.
+    rule "dfit":  stop after sweep n >= 2 when |Delta_n - Delta_{n-1}| < eps, Delta the fit of
+                  Eq. (cpfit) (Eq. canon, read with an absolute value); needs normR2.
+    rule "eta":   stop after sweep n >= 1 when eta_n < eps, Eq. (N3_stopping), eta_1 measured
+                  against the initial guess.
+    Returns (U, lam, hist, iterates) where iterates[k] are the factors after sweep k
+    (iterates[0] = the start), as dicts including "lam"."""
+    U = {m: np.array(U0[m], dtype=np.float64, copy=True) for m in MODES}
+    lam = np.ones(U["a"].shape[1]) if lam0 is None else np.array(lam0, dtype=np.float64)
+    iterates = [dict(U, lam=lam.copy())]
+    hist = []
+    for n in range(1, max_sweeps + 1):
+        Un, lamn, info = als_sweep(Bvv, tau, U, lam, normR2)
+        info["eta"] = eta(Un, lamn, U, lam)
+        hist.append(info)
+        U, lam = Un, lamn
+        iterates.append(dict(U, lam=lam.copy()))
+        if rule == "dfit" and n >= 2 and abs(hist[-1]["fit"] - hist[-2]["fit"]) < eps:
+            break
+        if rule == "eta" and info["eta"] < eps:
+            break
+    return U, lam, hist, iterates
+
+
+class NearOptimalGuess:
+    """The "Near-Optimal guess" of the Role of the Initial Guess section: when a CPD needs
+    n > 5 ALS iterations, the factors after iteration n - 5 are cached; otherwise the
+    previous cache is kept.  Every CPD after the first starts from the cache; the first
+    (and any CPD while no cache exists yet) starts from the random guess."""
+
+    OFFSET = 5
+
+    def __init__(self, random_guess: dict):
+        self.random_guess = {m: np.array(random_guess[m], copy=True) for m in MODES}
+        self.cache = None
+
+    def start(self) -> dict:
+        src = self.cache if self.cache is not None else self.random_guess
+        return {m: src[m].copy() for m in MODES}
+
+    def finish(self, iterates: list):
+        n = len(iterates) - 1
+        if n > self.OFFSET:
+            self.cache = {m: iterates[n - self.OFFSET][m].copy() for m in MODES}

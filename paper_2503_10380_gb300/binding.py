@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_PKG, "libpplcpd.so")
 
 PPL_OK, PPL_EINVAL, PPL_ENOMEM, PPL_ECUDA, PPL_ETIMEOUT, PPL_ENOTREADY = range(6)
 PREC = {"fp64": 0, "bf16x3": 1, "tf32": 2}
+STOP = {"fixed": 0, "dfit": 1, "eta": 2}
+GUESS = {"optimal": 0, "near_optimal": 1, "random": 2}
 MODE = {"a": 0, "b": 1, "i": 2, "j": 3}
 STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4: "PPL_ETIMEOUT",
                 5: "PPL_ENOTREADY"}
@@ -66,6 +68,9 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_stats_get.argtypes = [H, POINTER(ppl_cpd_stats)]
     L.ppl_cpd_phase_ms.argtypes = [H, POINTER(c_double)]
     L.ppl_cpd_factors_changed.argtypes = [H]
+    L.ppl_cpd_set_guess_policy.argtypes = [H, c_int]
+    L.ppl_cpd_reconstruct.argtypes = [H, c_void_p, c_int]
+    L.ppl_cpd_solve.argtypes = [H, c_int, c_int, c_double, POINTER(c_int), POINTER(c_double), POINTER(c_double)]
     L.ppl_last_error.argtypes = [H]
     L.ppl_last_error.restype = c_char_p
     L.ppl_cpd_destroy.argtypes = [H]
@@ -78,6 +83,7 @@ def lib() -> ctypes.CDLL:
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
+                 "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -154,6 +160,23 @@ def ppl_cpd_set_tau(h, tau_ptr):
 
 def ppl_cpd_factors_changed(h):
     _check(lib().ppl_cpd_factors_changed(h), h)
+
+
+def ppl_cpd_reconstruct(h, R_ptr, symmetrise: bool):
+    _check(lib().ppl_cpd_reconstruct(h, R_ptr, int(bool(symmetrise))), h)
+
+
+def ppl_cpd_set_guess_policy(h, policy):
+    _check(lib().ppl_cpd_set_guess_policy(h, GUESS[policy] if isinstance(policy, str) else int(policy)), h)
+
+
+def ppl_cpd_solve(h, max_sweeps: int, rule="fixed", eps: float = 0.0):
+    n = c_int(0)
+    fits = (c_double * max_sweeps)()
+    etas = (c_double * max_sweeps)()
+    _check(lib().ppl_cpd_solve(h, max_sweeps, STOP[rule] if isinstance(rule, str) else int(rule), float(eps),
+                               ctypes.byref(n), fits, etas), h)
+    return n.value, list(fits)[:n.value], list(etas)[:n.value]
 
 
 def ppl_cpd_stats_get(h) -> dict:
@@ -272,6 +295,19 @@ class CpAls:
         for m in ("a", "b", "i", "j"):
             f[m].copy_(self.torch.as_tensor(factors[m], dtype=self.torch.float64))
         ppl_cpd_factors_changed(self.h)
+
+    def solve(self, max_sweeps: int, rule="fixed", eps: float = 0.0):
+        """One CPD under a stopping rule; returns (sweeps, fit history, eta history)."""
+        return ppl_cpd_solve(self.h, max_sweeps, rule, eps)
+
+    def reconstruct(self, symmetrise: bool = False):
+        """R~ (or its symmetrised form) as a [v][v][o][o] FP64 device tensor."""
+        out = self.torch.empty((self.v, self.v, self.o, self.o), dtype=self.torch.float64, device=self.B.device)
+        ppl_cpd_reconstruct(self.h, out.data_ptr(), symmetrise)
+        return out
+
+    def set_guess_policy(self, policy):
+        ppl_cpd_set_guess_policy(self.h, policy)
 
     def stats(self) -> dict:
         return ppl_cpd_stats_get(self.h)

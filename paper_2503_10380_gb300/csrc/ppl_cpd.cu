@@ -33,6 +33,9 @@ struct Layout {
     size_t T64, W64, Y64, S64;                       // FP64 form
     size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Za, Zb, gov, Gblk, Rblk;
+    size_t ring, cache, guess0;   // 6 iterates, the Near-Optimal cache, the initial guess
+    size_t recon;                 // Khatri-Rao chunks for the reconstruction
+    int rcr;
     size_t total;
     int rc, na;
     long long ldv, ldX, ldo2, ldvv;
@@ -98,6 +101,12 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.gov = take((size_t)o * v * o * v * d);
     L.Gblk = take((size_t)na * v3 * d);
     L.Rblk = take((size_t)na * v * o * o * d);
+    const size_t fsz = (size_t)(2 * v + 2 * o + 1) * R * d;
+    L.ring = take(6 * fsz);
+    L.cache = take(fsz);
+    L.guess0 = take(fsz);
+    L.rcr = R < 64 ? R : 64;
+    L.recon = take((size_t)((long long)v * v + (long long)o * o) * L.rcr * d);
     const size_t none = (size_t)-1;
     L.T64 = L.W64 = L.Y64 = L.S64 = none;
     L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
@@ -156,6 +165,10 @@ struct ppl_cpd {
     cudaEvent_t pev[9];
     bool have_pev;
     long long kernels_per_sweep;
+    int guess_policy;
+    bool cache_valid;
+    long long nsolves;
+    size_t fac_bytes() const { return (size_t)(2 * v + 2 * o + 1) * R * sizeof(double); }
 
     template <class T>
     T* at(size_t off) const { return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(ws + off); }
@@ -630,6 +643,16 @@ int sweep_body(ppl_cpd* h) {
     return check_cuda(h, "sweep");
 }
 
+// the factor buffer holds a new guess: lam = 1, Gram matrices, ||R~_0||^2 (on h->st)
+void refresh_factors(ppl_cpd* h) {
+    fill_f64(h->lam, (size_t)h->R, 1.0, h->st);
+    for (int m = 0; m < 4; ++m) gram(h, m);
+    fit_terms(h->at<double>(h->L.M), h->U[0], h->lam, 0, h->R, h->G(0), h->G(1), h->G(2), h->G(3),
+              h->at<double>(h->L.partial), h->scal() + SC_TERMS, h->st);
+    cudaMemcpyAsync(h->scal() + SC_NORM2_PREV, h->scal() + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice,
+                    h->st);
+}
+
 int enter(ppl_cpd* h) {
     cudaEventRecord(h->ev_in, h->user);
     cudaStreamWaitEvent(h->st, h->ev_in, 0);
@@ -720,6 +743,9 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     for (double& x : h->last_hist) x = nan("");
     h->have_pev = false;
     h->kernels_per_sweep = 0;
+    h->guess_policy = PPL_GUESS_OPTIMAL;
+    h->cache_valid = false;
+    h->nsolves = 0;
     if (op.profile) {
         for (int k = 0; k < 9; ++k)
             if (cudaEventCreate(&h->pev[k]) != cudaSuccess) {
@@ -741,6 +767,7 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
         cudaMemsetAsync(h->ws + L.scal, 0, NSCAL * sizeof(double), h->st);
         cudaMemsetAsync(h->ws + L.flags, 0, 64, h->st);
         fill_f64(h->lam, (size_t)R, 1.0, h->st);
+        cudaMemcpyAsync(h->ws + L.guess0, h->fac, h->fac_bytes(), cudaMemcpyDeviceToDevice, h->st);
         for (int m = 0; m < 4; ++m) gram(h, m);
         // ||R~_0||^2 of the initial guess (eta's first denominator)
         fit_terms(h->at<double>(h->L.M), h->U[0], h->lam, 0, R, h->G(0), h->G(1), h->G(2), h->G(3),
@@ -931,6 +958,32 @@ int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_ou
     return PPL_OK;
 }
 
+int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise) {
+    if (!h || !R_out) return fail(h, PPL_EINVAL, "NULL argument");
+    const int o = h->o, v = h->v, R = h->R, rcr = h->L.rcr;
+    int e = enter(h);
+    if (e) return e;
+    double* Kab = h->at<double>(h->L.recon);
+    double* Kij = Kab + (size_t)v * v * rcr;
+    for (int r0 = 0; r0 < R; r0 += rcr) {
+        const int rc = (R - r0 < rcr) ? R - r0 : rcr;
+        kr_pair(h->U[0], h->U[1], h->lam, v, v, R, r0, rc, Kab, h->st);
+        kr_pair(h->U[2], h->U[3], nullptr, o, o, R, r0, rc, Kij, h->st);
+        G64 g{};
+        g.A = Kab; g.am = ix1(rc); g.ak = ix1(1);
+        g.B = Kij; g.bn = ix1(rc); g.bk = ix1(1);
+        g.C = R_out; g.cm = ix1((long long)o * o); g.cn = ix1(1);
+        g.M = v * v; g.N = o * o; g.K = rc; g.batch = 1; g.ksplit = 1;
+        g.alpha = 1.0; g.beta = (r0 == 0) ? 0.0 : 1.0;
+        gemm64(g, h->st);
+    }
+    if (symmetrise) symmetrise_pairs(R_out, v, o, h->st);
+    e = check_cuda(h, "reconstruct");
+    if (!e) e = sync_and_check(h);
+    leave(h);
+    return e;
+}
+
 int ppl_cpd_set_tau(ppl_cpd* h, const double* tau) {
     if (!h || !tau) return fail(h, PPL_EINVAL, "NULL argument");
     const bool same = (tau == h->tau);
@@ -959,16 +1012,69 @@ int ppl_cpd_factors_changed(ppl_cpd* h) {
     if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
     int e = enter(h);
     if (e) return e;
-    fill_f64(h->lam, (size_t)h->R, 1.0, h->st);
-    for (int m = 0; m < 4; ++m) gram(h, m);
-    fit_terms(h->at<double>(h->L.M), h->U[0], h->lam, 0, h->R, h->G(0), h->G(1), h->G(2), h->G(3),
-              h->at<double>(h->L.partial), h->scal() + SC_TERMS, h->st);
-    cudaMemcpyAsync(h->scal() + SC_NORM2_PREV, h->scal() + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice,
-                    h->st);
+    refresh_factors(h);
     e = check_cuda(h, "factors_changed");
     if (!e) e = sync_and_check(h);
     leave(h);
     return e;
+}
+
+int ppl_cpd_set_guess_policy(ppl_cpd* h, int policy) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (policy < PPL_GUESS_OPTIMAL || policy > PPL_GUESS_RANDOM) return fail(h, PPL_EINVAL, "unknown policy %d", policy);
+    h->guess_policy = policy;
+    return PPL_OK;
+}
+
+int ppl_cpd_solve(ppl_cpd* h, int max_sweeps, int stop_rule, double eps, int* sweeps_done, double* fit_hist,
+                  double* eta_hist) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (max_sweeps < 1) return fail(h, PPL_EINVAL, "max_sweeps < 1");
+    if (stop_rule < PPL_STOP_FIXED || stop_rule > PPL_STOP_ETA) return fail(h, PPL_EINVAL, "unknown stop rule");
+    if (stop_rule == PPL_STOP_ETA && !h->opts.want_eta) return fail(h, PPL_EINVAL, "PPL_STOP_ETA needs want_eta");
+    if (stop_rule == PPL_STOP_DFIT && !h->have_normR2) return fail(h, PPL_ENOTREADY, "PPL_STOP_DFIT needs ||R||^2");
+    int e = enter(h);
+    if (e) return e;
+    const size_t fb = h->fac_bytes();
+    if (h->nsolves > 0 && h->guess_policy != PPL_GUESS_OPTIMAL) {
+        const size_t src = (h->guess_policy == PPL_GUESS_NEAR_OPTIMAL && h->cache_valid) ? h->L.cache : h->L.guess0;
+        cudaMemcpyAsync(h->fac, h->ws + src, fb, cudaMemcpyDeviceToDevice, h->st);
+        refresh_factors(h);
+    }
+    cudaMemcpyAsync(h->ws + h->L.ring, h->fac, fb, cudaMemcpyDeviceToDevice, h->st);   // iterate 0
+    e = leave(h);
+    if (e) return e;
+    double prev_fit = nan("");
+    int n = 0;
+    for (n = 1; n <= max_sweeps; ++n) {
+        double fit = 0.0;
+        e = ppl_cpd_sweep(h, 1, &fit);
+        if (e) return e;
+        if (fit_hist) fit_hist[n - 1] = fit;
+        if (eta_hist) eta_hist[n - 1] = h->last_hist[3];
+        if ((e = enter(h))) return e;
+        cudaMemcpyAsync(h->ws + h->L.ring + (size_t)(n % 6) * fb, h->fac, fb, cudaMemcpyDeviceToDevice, h->st);
+        if ((e = leave(h))) return e;
+        bool stop = false;
+        if (stop_rule == PPL_STOP_DFIT && n >= 2 && fabs(fit - prev_fit) < eps) stop = true;
+        if (stop_rule == PPL_STOP_ETA && h->last_hist[3] < eps) stop = true;
+        prev_fit = fit;
+        if (stop) break;
+    }
+    if (n > max_sweeps) n = max_sweeps;
+    if (h->guess_policy == PPL_GUESS_NEAR_OPTIMAL && n > 5) {
+        if ((e = enter(h))) return e;
+        cudaMemcpyAsync(h->ws + h->L.cache, h->ws + h->L.ring + (size_t)((n - 5) % 6) * fb, fb,
+                        cudaMemcpyDeviceToDevice, h->st);
+        e = check_cuda(h, "solve");
+        if (!e) e = sync_and_check(h);
+        leave(h);
+        if (e) return e;
+        h->cache_valid = true;
+    }
+    h->nsolves++;
+    if (sweeps_done) *sweeps_done = n;
+    return PPL_OK;
 }
 
 int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {

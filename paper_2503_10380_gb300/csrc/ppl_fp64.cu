@@ -281,6 +281,35 @@ __global__ void __launch_bounds__(RB) k_exact_reduce(const double* Rblk, int a0,
     if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = sE;
 }
 
+__global__ void k_kr_pair(const double* U1, const double* U2, const double* lam, int d1, int d2, int R, int r0,
+                          int rc, double* out) {
+    const long long total = (long long)d1 * d2 * rc;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % rc);
+        const long long pq = e / rc;
+        const int p = (int)(pq / d2), q = (int)(pq % d2);
+        double x = U1[(long long)p * R + r0 + r] * U2[(long long)q * R + r0 + r];
+        if (lam) x *= lam[r0 + r];
+        out[e] = x;
+    }
+}
+
+__global__ void k_symmetrise(double* X, int v, int o) {
+    const long long oo = (long long)o * o, total = (long long)v * v * oo;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % o), i = (int)((e / o) % o);
+        const int b = (int)((e / oo) % v), a = (int)(e / (oo * v));
+        const long long f = (((long long)b * v + a) * o + j) * o + i;
+        if (e < f) {
+            const double m = 0.5 * (X[e] + X[f]);
+            X[e] = m;
+            X[f] = m;
+        }
+    }
+}
+
 __global__ void k_fill(double* p, size_t n, double val) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         p[e] = val;
@@ -360,6 +389,15 @@ void exact_reduce(const double* Rblk, int a0, int na, int v, int o, const double
 
 void sum_partials(const double* partial, int n, double* out, int accumulate, cudaStream_t s) {
     k_sum_partials<<<1, RB, 0, s>>>(partial, n, 1, out, accumulate);
+}
+
+void kr_pair(const double* U1, const double* U2, const double* lam, int d1, int d2, int R, int r0, int rc,
+             double* out, cudaStream_t s) {
+    k_kr_pair<<<grid_for((long long)d1 * d2 * rc, 256), 256, 0, s>>>(U1, U2, lam, d1, d2, R, r0, rc, out);
+}
+
+void symmetrise_pairs(double* X, int v, int o, cudaStream_t s) {
+    k_symmetrise<<<grid_for((long long)v * v * o * o, 256), 256, 0, s>>>(X, v, o);
 }
 
 void fill_f64(double* p, size_t n, double val, cudaStream_t s) {

@@ -59,6 +59,11 @@ void energy_reduce(const double* Za, const double* Zb, const double* Ui, const d
 void exact_reduce(const double* Rblk, int a0, int na, int v, int o, const double* g,
                   double* partial, double* acc, cudaStream_t s);
 void sum_partials(const double* partial, int n, double* out, int accumulate, cudaStream_t s);
+// out[(p*d2 + q)][r'] = U1[p][r0+r'] U2[q][r0+r'] (lam[r0+r'] if lam), r' < rc; out row stride rc
+void kr_pair(const double* U1, const double* U2, const double* lam, int d1, int d2, int R, int r0, int rc,
+             double* out, cudaStream_t s);
+// X[a][b][i][j] <- 0.5 (X[a][b][i][j] + X[b][a][j][i]) in place
+void symmetrise_pairs(double* X, int v, int o, cudaStream_t s);
 void fill_f64(double* p, size_t n, double val, cudaStream_t s);
 
 // ---- tensor-core path (ppl_tc.cu) ------------------------------------------

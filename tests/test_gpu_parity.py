@@ -187,3 +187,45 @@ def test_factors_changed_restarts_from_new_guess():
     for m in orc.MODES:
         assert _rel(f[m], U_ref[m]) < 1e-9
     cp.close()
+
+
+@pytest.mark.parametrize("rule,eps", [("eta", 0.05), ("dfit", 1e-3)])
+def test_solve_sequence_near_optimal_matches_oracle(rule, eps):
+    """A CC-like sequence tau_k (k = 0..3), one CPD per tau with a stopping rule,
+    Near-Optimal guesses between CPDs: sweep counts and final factors equal the oracle's."""
+    inp = inputs.make_inputs(4, 14, 20, 24, seed=9)
+    taus = [inp.tau]
+    for k in range(1, 4):
+        taus.append(taus[-1] + inputs.tau_increment(inp.tau, k, seed=9))
+    pol = orc.NearOptimalGuess(inp.factors)
+    cp = binding.CpAls(_dev(inp.B), _dev(taus[0]), inp.factors, precision="fp64", want_eta=True)
+    cp.set_guess_policy("near_optimal")
+    tau_dev = [_dev(t) for t in taus]
+    for k, t in enumerate(taus):
+        if k:
+            cp.set_tau(tau_dev[k])
+        n2 = float(np.sum(orc.ppl_tensor(inp.Bvv, t) ** 2))
+        cp.set_normR2(n2)
+        U0 = pol.start()
+        U_ref, lam_ref, hist, its = orc.cp_solve(inp.Bvv, t, U0, 40, rule, eps, n2)
+        pol.finish(its)
+        n, fits, etas = cp.solve(40, rule, eps)
+        assert n == len(hist), (k, n, len(hist))
+        f = {m: x.cpu().numpy() for m, x in cp.factors().items()}
+        for m in orc.MODES:
+            assert _rel(f[m], U_ref[m]) < 1e-8
+    cp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_reconstruct_and_symmetrise(prec):
+    inp = inputs.make_inputs(3, 13, 17, 70, seed=12)     # R spans two reconstruction chunks
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec)
+    cp.sweep(2)
+    f = {k: t.cpu().numpy() for k, t in cp.factors().items()}
+    R_ref = orc.reconstruct(f, f["lam"])
+    assert _rel(cp.reconstruct(False).cpu().numpy(), R_ref) < 1e-13
+    S = cp.reconstruct(True).cpu().numpy()
+    assert _rel(S, orc.symmetrise(R_ref)) < 1e-13
+    assert _rel(S, S.transpose(1, 0, 3, 2)) < 1e-15
+    cp.close()

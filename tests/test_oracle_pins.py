@@ -317,3 +317,33 @@ def test_generator_distribution_moments():
 def test_batch_shapes_in_range():
     for o, v, X, R in inputs.batch_shapes(64, seed=0):
         assert 4 <= o <= 24 and 40 <= v <= 240 and X == 3 * v and 2 * v <= R <= 4 * v
+
+
+# ---------------------------------------------------------------- stopping rules, guesses
+
+def test_stopping_rules_fire_on_their_definitions(tiny):
+    Rt = orc.ppl_tensor(tiny.Bvv, tiny.tau)
+    n2 = float(np.sum(Rt * Rt))
+    _, _, hist, it = orc.cp_solve(tiny.Bvv, tiny.tau, tiny.factors, 60, "dfit", 1e-3, n2)
+    n = len(hist)
+    assert abs(hist[-1]["fit"] - hist[-2]["fit"]) < 1e-3
+    assert all(abs(hist[k]["fit"] - hist[k - 1]["fit"]) >= 1e-3 for k in range(1, n - 1))
+    _, _, hist, it = orc.cp_solve(tiny.Bvv, tiny.tau, tiny.factors, 60, "eta", 0.02418, n2)
+    assert hist[-1]["eta"] < 0.02418 and all(h["eta"] >= 0.02418 for h in hist[:-1])
+    # eta of each iterate against the previous one, from the formed tensors
+    R1 = orc.reconstruct(it[-1], it[-1]["lam"])
+    R0 = orc.reconstruct(it[-2], it[-2]["lam"])
+    assert abs(hist[-1]["eta"] - np.linalg.norm(R1 - R0) / np.linalg.norm(R0)) < 1e-10
+    _, _, hist, it = orc.cp_solve(tiny.Bvv, tiny.tau, tiny.factors, 7, "fixed")
+    assert len(hist) == 7 and len(it) == 8
+
+
+def test_near_optimal_cache_follows_the_offset_rule():
+    guess = {m: np.full((2, 1), float(k)) for k, m in enumerate(orc.MODES)}
+    pol = orc.NearOptimalGuess(guess)
+    assert np.array_equal(pol.start()["b"], guess["b"])           # first CPD: random guess
+    its = [{m: np.full((2, 1), 100.0 + s) for m in orc.MODES} for s in range(9)]   # n = 8 sweeps
+    pol.finish(its)
+    assert np.array_equal(pol.start()["a"], its[3]["a"])           # iterate n - 5 = 3
+    pol.finish(its[:5])                                             # n = 4 <= 5: cache kept
+    assert np.array_equal(pol.start()["j"], its[3]["j"])
