@@ -178,6 +178,29 @@ int ppl_cpd_solve(ppl_cpd* h, int max_sweeps, int stop_rule, double eps, int* sw
  * ppl_cpd_init): recompute the Gram matrices the solves use and reset lam to 1. */
 int ppl_cpd_factors_changed(ppl_cpd* h);
 
+/* ---- autotuning and batches of uneven instances ----------------------------------- */
+
+/* Time the MTTKRP chain of this handle for candidate r-chunk sizes (multiples of
+ * 16 up to the size its workspace was planned for) and keep the fastest for all
+ * later sweeps.  r_chunk_out (host, may be NULL) receives the choice.  Call it
+ * before the first sweep (a captured sweep graph is discarded). */
+int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out);
+
+typedef struct ppl_cpd_batch ppl_cpd_batch;   /* opaque, host memory owned by the library */
+
+/* Group n handles (each from ppl_cpd_init with its own workspace, sizes may
+ * differ) so that one sweep of every instance runs from a single CUDA graph:
+ * instance k is issued on internal stream k % nstreams, all forked from and
+ * joined back to `stream`.  The handles stay owned by the caller and must
+ * outlive the batch. */
+int ppl_cpd_batch_create(ppl_cpd_batch** b, int n, ppl_cpd* const* handles, int nstreams, void* stream);
+
+/* nsweeps sweeps of every instance; fits (HOST, may be NULL) receives
+ * [nsweeps][n] fit values (NaN where ||R||^2 is unknown). */
+int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits);
+
+int ppl_cpd_batch_destroy(ppl_cpd_batch* b);
+
 /* Counters and the last sweep's scalars. */
 int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* stats);
 

@@ -70,6 +70,10 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_factors_changed.argtypes = [H]
     L.ppl_cpd_set_guess_policy.argtypes = [H, c_int]
     L.ppl_cpd_reconstruct.argtypes = [H, c_void_p, c_int]
+    L.ppl_cpd_autotune.argtypes = [H, POINTER(c_int)]
+    L.ppl_cpd_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int, c_void_p]
+    L.ppl_cpd_batch_sweep.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.ppl_cpd_batch_destroy.argtypes = [c_void_p]
     L.ppl_cpd_solve.argtypes = [H, c_int, c_int, c_double, POINTER(c_int), POINTER(c_double), POINTER(c_double)]
     L.ppl_last_error.argtypes = [H]
     L.ppl_last_error.restype = c_char_p
@@ -83,7 +87,8 @@ def lib() -> ctypes.CDLL:
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
-                 "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct",
+                 "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct", "ppl_cpd_autotune",
+                 "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -164,6 +169,55 @@ def ppl_cpd_factors_changed(h):
 
 def ppl_cpd_reconstruct(h, R_ptr, symmetrise: bool):
     _check(lib().ppl_cpd_reconstruct(h, R_ptr, int(bool(symmetrise))), h)
+
+
+def ppl_cpd_autotune(h) -> int:
+    rc = c_int(0)
+    _check(lib().ppl_cpd_autotune(h, ctypes.byref(rc)), h)
+    return rc.value
+
+
+def ppl_cpd_batch_create(handles, nstreams, stream_ptr):
+    arr = (c_void_p * len(handles))(*[h.value if isinstance(h, c_void_p) else h for h in handles])
+    b = c_void_p()
+    _check(lib().ppl_cpd_batch_create(ctypes.byref(b), len(handles), arr, nstreams, stream_ptr))
+    return b
+
+
+def ppl_cpd_batch_sweep(b, nsweeps, n_instances, want_fits=True):
+    buf = (c_double * (max(nsweeps, 1) * n_instances))() if want_fits else None
+    _check(lib().ppl_cpd_batch_sweep(b, nsweeps, buf))
+    if not want_fits:
+        return None
+    return [list(buf)[k * n_instances:(k + 1) * n_instances] for k in range(nsweeps)]
+
+
+def ppl_cpd_batch_destroy(b):
+    _check(lib().ppl_cpd_batch_destroy(b))
+
+
+class Batch:
+    """Several CpAls problems swept together from one CUDA graph."""
+
+    def __init__(self, problems, nstreams=8):
+        import torch
+        self.problems = list(problems)
+        self.b = ppl_cpd_batch_create([p.h for p in self.problems], nstreams,
+                                      torch.cuda.current_stream().cuda_stream)
+
+    def sweep(self, n=1, want_fits=True):
+        return ppl_cpd_batch_sweep(self.b, n, len(self.problems), want_fits)
+
+    def close(self):
+        if self.b:
+            ppl_cpd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ppl_cpd_set_guess_policy(h, policy):
@@ -305,6 +359,10 @@ class CpAls:
         out = self.torch.empty((self.v, self.v, self.o, self.o), dtype=self.torch.float64, device=self.B.device)
         ppl_cpd_reconstruct(self.h, out.data_ptr(), symmetrise)
         return out
+
+    def autotune(self) -> int:
+        """Time candidate r-chunk sizes and keep the fastest; returns it."""
+        return ppl_cpd_autotune(self.h)
 
     def set_guess_policy(self, policy):
         ppl_cpd_set_guess_policy(self.h, policy)

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ppl_cpd.h"
 
@@ -1077,6 +1078,61 @@ int ppl_cpd_solve(ppl_cpd* h, int max_sweeps, int stop_rule, double eps, int* sw
     return PPL_OK;
 }
 
+int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    const int planned = h->L.rc;
+    const int step = h->tc() ? 16 : 1;
+    std::vector<int> cand;
+    const int base[] = {48, 64, 96, 128, 160, 208, 256};
+    for (int c : base) {
+        const int cc = (c / step) * step;
+        if (cc >= step && cc < planned) cand.push_back(cc);
+    }
+    cand.push_back(planned);
+    int e = enter(h);
+    if (e) return e;
+    double* M = h->at<double>(h->L.M);
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    if (h->tc()) e = t_tc(h);
+    else t_fp64(h);
+    float best_ms = 1e30f;
+    int best = planned;
+    for (int c : cand) {
+        h->L.rc = c;
+        for (int rep = 0; rep < 2 && !e; ++rep) {   // the first pass warms up
+            cudaEventRecord(t0, h->st);
+            if (h->tc()) e = chain_tc(h, 0, M);
+            else mttkrp_ab_fp64(h, 0, M);
+            cudaEventRecord(t1, h->st);
+        }
+        if (e) break;
+        if (cudaEventSynchronize(t1) != cudaSuccess) { e = check_cuda(h, "autotune"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    h->L.rc = e ? planned : best;
+    if (!e) e = check_cuda(h, "autotune");
+    if (!e) e = sync_and_check(h);
+    leave(h);
+    if (h->graph_ready) {
+        cudaGraphExecDestroy(h->gexec);
+        cudaGraphDestroy(h->graph);
+        h->gexec = nullptr;
+        h->graph = nullptr;
+        h->graph_ready = false;
+    }
+    if (!e && r_chunk_out) *r_chunk_out = h->L.rc;
+    return e;
+}
+
 int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
     if (!h || !s) return fail(h, PPL_EINVAL, "NULL argument");
     unsigned long long nc = 0;
@@ -1096,6 +1152,138 @@ int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
 }
 
 const char* ppl_last_error(const ppl_cpd* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"
+
+struct ppl_cpd_batch {
+    std::vector<ppl_cpd*> hs;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaStream_t user, origin;
+    cudaEvent_t fork, ev_in, ev_out;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool ready;
+};
+
+extern "C" {
+
+int ppl_cpd_batch_create(ppl_cpd_batch** bp, int n, ppl_cpd* const* handles, int nstreams, void* stream) {
+    if (!bp || n < 1 || !handles || nstreams < 1) return fail(nullptr, PPL_EINVAL, "bad batch arguments");
+    for (int k = 0; k < n; ++k)
+        if (!handles[k]) return fail(nullptr, PPL_EINVAL, "handle %d is NULL", k);
+    ppl_cpd_batch* b = new (std::nothrow) ppl_cpd_batch();
+    if (!b) return fail(nullptr, PPL_EINVAL, "out of host memory");
+    b->hs.assign(handles, handles + n);
+    b->user = (cudaStream_t)stream;
+    b->graph = nullptr;
+    b->exec = nullptr;
+    b->ready = false;
+    bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    const int ns = nstreams < n ? nstreams : n;
+    for (int i = 0; ok && i < ns; ++i) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) {
+            b->streams.push_back(s);
+            b->joins.push_back(e);
+        }
+    }
+    if (!ok) {
+        cudaGetLastError();
+        ppl_cpd_batch_destroy(b);
+        return fail(nullptr, PPL_ECUDA, "could not create the batch streams/events");
+    }
+    *bp = b;
+    return PPL_OK;
+}
+
+int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
+    if (!b || nsweeps < 0) return fail(nullptr, PPL_EINVAL, "bad batch arguments");
+    const int n = (int)b->hs.size();
+    cudaEventRecord(b->ev_in, b->user);
+    cudaStreamWaitEvent(b->origin, b->ev_in, 0);
+    if (!b->ready) {
+        cudaError_t ce = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch capture: %s", cudaGetErrorString(ce));
+        cudaEventRecord(b->fork, b->origin);
+        int err = PPL_OK;
+        for (size_t i = 0; i < b->streams.size(); ++i) cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        for (int k = 0; k < n && !err; ++k) {
+            ppl_cpd* h = b->hs[k];
+            cudaStream_t keep = h->st;
+            h->st = b->streams[k % b->streams.size()];
+            err = sweep_body(h);
+            h->st = keep;
+            if (err) g_err = h->err;
+        }
+        for (size_t i = 0; i < b->streams.size(); ++i) {
+            cudaEventRecord(b->joins[i], b->streams[i]);
+            cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+        }
+        cudaGraph_t gr = nullptr;
+        ce = cudaStreamEndCapture(b->origin, &gr);
+        if (err) {
+            if (gr) cudaGraphDestroy(gr);
+            return err;
+        }
+        if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch end capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->exec, gr, 0);
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(gr);
+            return fail(nullptr, PPL_ECUDA, "batch instantiate: %s", cudaGetErrorString(ce));
+        }
+        b->graph = gr;
+        b->ready = true;
+    }
+    for (int s = 0; s < nsweeps; ++s) {
+        if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess)
+            return fail(nullptr, PPL_ECUDA, "batch launch: %s", cudaGetErrorString(cudaGetLastError()));
+        if (fits || s == nsweeps - 1) {
+            if (cudaStreamSynchronize(b->origin) != cudaSuccess)
+                return fail(nullptr, PPL_ECUDA, "batch sync: %s", cudaGetErrorString(cudaGetLastError()));
+            for (int k = 0; k < n; ++k) {
+                ppl_cpd* h = b->hs[k];
+                unsigned int flag = 0;
+                cudaMemcpy(&flag, h->errflag(), sizeof flag, cudaMemcpyDeviceToHost);
+                if (flag) {
+                    cudaMemset(h->errflag(), 0, sizeof flag);
+                    return fail(nullptr, PPL_ETIMEOUT, "instance %d: a bounded device wait expired (0x%x)", k, flag);
+                }
+                double hist[4];
+                cudaMemcpy(hist, h->at<double>(h->L.hist), sizeof hist, cudaMemcpyDeviceToHost);
+                for (int q = 0; q < 4; ++q) h->last_hist[q] = hist[q];
+                if (fits) fits[(size_t)s * n + k] = hist[0];
+            }
+        }
+        for (int k = 0; k < n; ++k) b->hs[k]->sweeps++;
+    }
+    cudaEventRecord(b->ev_out, b->origin);
+    cudaStreamWaitEvent(b->user, b->ev_out, 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch: %s", cudaGetErrorString(e));
+    return PPL_OK;
+}
+
+int ppl_cpd_batch_destroy(ppl_cpd_batch* b) {
+    if (!b) return PPL_OK;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    delete b;
+    return PPL_OK;
+}
 
 int ppl_cpd_destroy(ppl_cpd* h) {
     if (!h) return PPL_OK;

@@ -507,13 +507,22 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
         if (sms <= 0 || per <= 0) return -1;
         g_solve_grid = sms;   // one block per SM: the look-ahead block keeps its SM's FP64 pipe
     }
+    // small problems take fewer blocks (enough for the first step's tiles and
+    // panel rows), so that several instances' solves can share the GPU
+    const int t0 = (R > NB) ? (R - NB + NB - 1) / NB : 0;
+    const int d = (dim + NB - 1) / NB;
+    int want = t0 * (t0 + 1) / 2 + d * t0;
+    const int ptask = (R - (R < NB ? R : NB) + dim + 7) / 8;
+    if (ptask > want) want = ptask;
+    if (want < 8) want = 8;
+    const int grid = want < g_solve_grid ? want : g_solve_grid;
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
     SolveP p;
     p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.U = U; p.lam = lam; p.G = G;
     p.sync = sync; p.maxdiag = maxdiag; p.nclamp = nclamp; p.err = err; p.R = R; p.dim = dim;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_solve_grid);
+    cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;

@@ -229,3 +229,39 @@ def test_reconstruct_and_symmetrise(prec):
     assert _rel(S, orc.symmetrise(R_ref)) < 1e-13
     assert _rel(S, S.transpose(1, 0, 3, 2)) < 1e-15
     cp.close()
+
+
+def test_batch_of_uneven_instances_equals_individual_sweeps():
+    shapes = [(4, 40, 120, 96), (6, 56, 168, 130), (5, 24, 72, 48), (8, 64, 192, 200)]
+    probs, solo = [], []
+    inps = [inputs.make_inputs(*sh, seed=20 + k) for k, sh in enumerate(shapes)]
+    for inp in inps:
+        probs.append(binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3"))
+        solo.append(binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3"))
+    batch = binding.Batch(probs, nstreams=3)
+    batch.sweep(3)
+    for p, q in zip(probs, solo):
+        q.sweep(3)
+        fp = {k: t.cpu().numpy() for k, t in p.factors().items()}
+        fq = {k: t.cpu().numpy() for k, t in q.factors().items()}
+        for k in fp:
+            assert _rel(fp[k], fq[k]) < 1e-12, k
+    batch.close()
+    for p in probs + solo:
+        p.close()
+
+
+def test_autotune_picks_a_chunk_and_keeps_results():
+    inp = inputs.make_inputs(6, 48, 144, 300, seed=30)
+    a = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3")
+    rc = a.autotune()
+    assert 16 <= rc <= 256 and rc % 16 == 0
+    b = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3")
+    a.sweep(2)
+    b.sweep(2)
+    fa = {k: t.cpu().numpy() for k, t in a.factors().items()}
+    fb = {k: t.cpu().numpy() for k, t in b.factors().items()}
+    for k in fa:
+        assert _rel(fa[k], fb[k]) < 1e-4
+    a.close()
+    b.close()
