@@ -353,6 +353,107 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, world, rank, local):
+    """64 uneven instances (o in [4,24], v in [40,240], X = 3v, R in [2v,4v]) swept
+    together from one CUDA graph; one step = one sweep of every instance."""
+    import numpy as np
+    import torch
+    from paper_2503_10380_gb300 import binding, inputs
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    shapes = inputs.batch_shapes(64, seed=SEED)
+    data = [inputs.make_inputs_torch(*sh, seed=SEED + k, device=dev) for k, sh in enumerate(shapes)]
+    flops = sum(alg_flops(*sh) for sh in shapes)
+    probs = []
+    for (B, tau, fac) in data:
+        cp = binding.CpAls(B, tau, fac, precision=args.precision)
+        cp.autotune()
+        probs.append(cp)
+    batch = binding.Batch(probs, nstreams=8)
+    batch.sweep(args.warmup, want_fits=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    batch.sweep(args.steps, want_fits=False)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    launches = sum(p.stats()["kernels_per_sweep"] for p in probs)
+    # plain FP64 form of the same batch
+    f64 = [binding.CpAls(B, tau, fac, precision="fp64") for (B, tau, fac) in data]
+    fb = binding.Batch(f64, nstreams=8)
+    fb.sweep(1, want_fits=False)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    fb.sweep(2, want_fits=False)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    f64_ms = g0.elapsed_time(g1) / 2
+    fb.close()
+    for p in f64:
+        p.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # oracle sweeps over the first instances until ~15 s, scaled by flops to the batch
+        from oracle import ppl_oracle as orc
+        t_or, fl_or, k = 0.0, 0.0, 0
+        while t_or < 15.0 and k < len(shapes):
+            B, tau, fac = data[k]
+            o = shapes[k][0]
+            Bvv = np.ascontiguousarray(B.cpu().numpy()[:, o:, o:])
+            t = tau.cpu().numpy()
+            t0 = time.perf_counter()
+            orc.als_sweep(Bvv, t, fac, np.ones(shapes[k][3]))
+            t_or += time.perf_counter() - t0
+            fl_or += alg_flops(*shapes[k])
+            k += 1
+        cores, how = oracle_cores()
+        cpu = {"value": (fl_or / flops) / t_or, "unit": "batch sweeps/s", "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle sweep of each of the first {k} instances, scaled by flops to all 64; "
+                         f"threads from {how}"}
+    pk, pk_kind = peaks()
+    peak = pk["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+    tflops = flops / (ms / args.steps / 1000.0) / 1e12
+    value = world * args.steps / (ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "batch sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded; shapes of the paper's molecules)",
+        "config": {"workload": "cp-als-ppl batch of 64 uneven instances (o 4-24, v 40-240, X = 3v, R 2v-4v), one graph",
+                   "instances": 64, "precision": args.precision},
+        "sweep_tflops": tflops,
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": None, "kernel": "whole batch sweep (MTTKRP flops / sweep time)",
+                     "peak_source": f"{pk_kind}"},
+        "fp64_gpu": {"ms_per_sweep": f64_ms, "speedup_mixed_vs_fp64": f64_ms / (ms / args.steps)},
+        "gpu_launches": int(launches) * args.steps,
+        "clocks": {k2: ck[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "cpu_baseline": cpu,
+    }
+    batch.close()
+    for p in probs:
+        p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +463,8 @@ def main():
     ap.add_argument("--precision", choices=["bf16x3", "tf32"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="single: o=20 v=200 X=600 R=800 (default); batch: 64 uneven instances")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -373,6 +476,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "batch":
+            run_batch(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

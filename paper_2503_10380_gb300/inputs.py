@@ -156,3 +156,61 @@ def batch_shapes(count: int, seed: int = 0):
         R = 2 * v + int(u[k, 2] * (2 * v + 1))
         shapes.append((o, v, 3 * v, R))
     return shapes
+
+
+# --------------------------------------------------------------------------
+# the same generator in torch (for large sizes, on the device)
+# --------------------------------------------------------------------------
+
+def _i64(x: int) -> int:
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _lsr(torch, z, k: int):
+    """Logical right shift of int64 bit patterns."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix64_t(torch, z):
+    z = (z ^ _lsr(torch, z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr(torch, z, 27)) * _i64(0x94D049BB133111EB)
+    return z ^ _lsr(torch, z, 31)
+
+
+def uniform_t(torch, seed: int, stream: int, count: int, device, start: int = 0):
+    with np.errstate(over="ignore"):
+        key = int(_mix64(np.array([np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ (np.uint64(stream) * _STREAM_MUL)],
+                                  dtype=np.uint64))[0])
+    k = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    x = _mix64_t(torch, _i64(key) + k * _i64(int(_GAMMA)))
+    return _lsr(torch, x, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal_t(torch, seed: int, stream: int, count: int, device):
+    u = uniform_t(torch, seed, stream, 2 * count, device)
+    u1, u2 = u[0::2], u[1::2]
+    return torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
+
+
+def make_inputs_torch(o: int, v: int, X: int, R: int, seed: int = 0, device="cuda"):
+    """make_inputs with torch on `device`: returns (B, tau, factors) with B, tau
+    FP64 tensors on the device and the factors as numpy arrays.  Same recipe and
+    counter streams as make_inputs (values agree to rounding of log/cos and of
+    the sum over Q)."""
+    import torch
+    n = o + v
+    e_occ = -1.5 + 1.2 * uniform_t(torch, seed, STREAM_E_OCC, o, device)
+    e_vir = 0.1 + 2.9 * uniform_t(torch, seed, STREAM_E_VIR, v, device)
+    B = normal_t(torch, seed, STREAM_Z, X * n * n, device).view(X, n, n)
+    scale = SIGMA_B * torch.exp(-torch.arange(X, dtype=torch.float64, device=device) / DECAY_Q) / math.sqrt(2.0)
+    B = (B + B.transpose(1, 2)) * scale[:, None, None]
+    Bov = B[:, :o, o:].reshape(X, o * v)
+    g = (Bov.T @ Bov).view(o, v, o, v)
+    denom = (e_occ[:, None, None, None] + e_occ[None, None, :, None]
+             - e_vir[None, :, None, None] - e_vir[None, None, None, :])
+    tau = (g / denom).permute(0, 2, 1, 3).contiguous()
+    del g, denom
+    t1 = T1_SCALE * normal_t(torch, seed, STREAM_T1, o * v, device).view(o, v)
+    tau += t1[:, None, :, None] * t1[None, :, None, :]
+    return B.contiguous(), tau, make_factors(seed, o, v, R)

@@ -347,3 +347,13 @@ def test_near_optimal_cache_follows_the_offset_rule():
     assert np.array_equal(pol.start()["a"], its[3]["a"])           # iterate n - 5 = 3
     pol.finish(its[:5])                                             # n = 4 <= 5: cache kept
     assert np.array_equal(pol.start()["j"], its[3]["j"])
+
+
+def test_torch_generator_matches_numpy_generator():
+    torch = pytest.importorskip("torch")
+    a = inputs.make_inputs(3, 7, 5, 4, seed=13)
+    B, tau, f = inputs.make_inputs_torch(3, 7, 5, 4, seed=13, device="cpu")
+    assert np.max(np.abs(B.numpy() - a.B)) < 1e-14
+    assert np.max(np.abs(tau.numpy() - a.tau)) < 1e-12 * np.max(np.abs(a.tau))
+    for m in orc.MODES:
+        assert np.array_equal(f[m], a.factors[m])
