@@ -137,19 +137,33 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_from_profile():
-    """DRAM bytes per MTTKRP pass from the committed ncu summary, if it was
-    taken on the current tensor-core kernel source; else None."""
-    src = os.path.join(ROOT, "paper_2503_10380_gb300", "csrc", "ppl_tc.cu")
+def traffic_from_profile(key: str, src_name: str):
+    """DRAM bytes from the committed ncu summary (profiles/mttkrp_tc_cfg1_traffic.json)
+    if it was taken on the current source of the kernel; else None."""
+    src = os.path.join(ROOT, "paper_2503_10380_gb300", "csrc", src_name)
     prof = os.path.join(ROOT, "profiles", "mttkrp_tc_cfg1_traffic.json")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         d = json.load(open(prof))
-        if d.get("ppl_tc_sha256") == h:
-            return d.get("dram_bytes_per_sweep")
+        if d.get(src_name.replace(".cu", "") + "_sha256") == h:
+            return d.get(key)
     except Exception:
         pass
     return None
+
+
+def fp64_solve_flops(o, v, R):
+    """Algorithmic FP64 flops of the four mode updates of one sweep: per mode
+    2 R^3 / 3 (Cholesky) + 3 dim R^2 (forward and back substitution, Gram)."""
+    return 4 * (2.0 * R ** 3 / 3.0) + 3.0 * R * R * (2 * v + 2 * o)
+
+
+def fp64_peak_tflops(pk):
+    """FP64 FMA peak derived from ncu's sm__sass_thread_inst_executed_op_dfma_pred_on
+    peak_sustained = 2 per clock per SM: 2 FMA x 2 flops x SMs x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return 2 * 2 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def run_reference(args, world, rank):
@@ -317,7 +331,11 @@ def run_ours(args, world, rank, local):
     else:
         peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
         peak_note = "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25"
-    traffic = traffic_from_profile()
+    traffic_mttkrp = traffic_from_profile("dram_bytes_per_sweep", "ppl_tc.cu")
+    traffic_solve = traffic_from_profile("solve_bytes_per_launch", "ppl_solve.cu")
+    solve_ms = phases["solve_a"] + phases["solve_b"] + phases["solve_ij"]
+    solve_tflops = fp64_solve_flops(O, V, RANK) / (solve_ms / 1000.0) / 1e12
+    fp64_peak = fp64_peak_tflops(pk)
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -329,10 +347,16 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mttkrp_tflops": mttkrp_tflops,
         "phase_ms": phases,
-        "roofline": {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": mttkrp_tflops / peak, "traffic": traffic,
-                     "kernel": "k_tc_gemm (all MTTKRP contractions of one sweep)",
-                     "peak_source": f"{pk_kind}: {peak_note}"},
+        "roofline": {"bound": "alu", "achieved": solve_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": solve_tflops / fp64_peak, "traffic": traffic_solve,
+                     "kernel": "k_solve (FP64 mode updates, the dominant kernel: 4 launches per sweep)",
+                     "peak_source": "derived: 2 DFMA/clk/SM (ncu peak_sustained) x 2 flops x SMs x max SM clock",
+                     "work": "per sweep 4 x 2R^3/3 + 3 R^2 (2v + 2o) FP64 flops"},
+        "roofline_mttkrp": {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak, "unit": "TFLOP/s",
+                            "frac": mttkrp_tflops / peak, "traffic": traffic_mttkrp,
+                            "kernel": "k_tc_gemm and its helpers (all MTTKRP contractions of one sweep)",
+                            "peak_source": f"{pk_kind}: {peak_note}",
+                            "work": "per sweep 4 o^2 v^2 R + 16 X v^2 R algorithmic flops"},
         "fp64_gpu": {"ms_per_sweep": f64_ms, "sweeps_per_s": 1000.0 / f64_ms,
                      "speedup_mixed_vs_fp64": value / world / (1000.0 / f64_ms)},
         "accuracy": {"sweeps": n_cmp, "E_cp_mixed": E_mixed, "E_cp_fp64": E_f64,
@@ -393,7 +417,7 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = reduce_max(e0.elapsed_time(e1), world, dev)
-    launches = sum(p.stats()["kernels_per_sweep"] for p in probs)
+    launches = batch.kernels_per_sweep()
     # plain FP64 form of the same batch
     f64 = [binding.CpAls(B, tau, fac, precision="fp64") for (B, tau, fac) in data]
     fb = binding.Batch(f64, nstreams=8)

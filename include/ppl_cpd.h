@@ -199,6 +199,9 @@ int ppl_cpd_batch_create(ppl_cpd_batch** b, int n, ppl_cpd* const* handles, int 
  * [nsweeps][n] fit values (NaN where ||R||^2 is unknown). */
 int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits);
 
+/* Kernel nodes in the batch's captured sweep graph (0 before the first sweep). */
+int ppl_cpd_batch_kernels(ppl_cpd_batch* b, long long* kernels_per_sweep);
+
 int ppl_cpd_batch_destroy(ppl_cpd_batch* b);
 
 /* Counters and the last sweep's scalars. */

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int, c_void_p]
     L.ppl_cpd_batch_sweep.argtypes = [c_void_p, c_int, POINTER(c_double)]
     L.ppl_cpd_batch_destroy.argtypes = [c_void_p]
+    L.ppl_cpd_batch_kernels.argtypes = [c_void_p, POINTER(ctypes.c_longlong)]
     L.ppl_cpd_solve.argtypes = [H, c_int, c_int, c_double, POINTER(c_int), POINTER(c_double), POINTER(c_double)]
     L.ppl_last_error.argtypes = [H]
     L.ppl_last_error.restype = c_char_p
@@ -88,7 +89,7 @@ def lib() -> ctypes.CDLL:
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
                  "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct", "ppl_cpd_autotune",
-                 "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy",
+                 "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy", "ppl_cpd_batch_kernels",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -207,6 +208,11 @@ class Batch:
 
     def sweep(self, n=1, want_fits=True):
         return ppl_cpd_batch_sweep(self.b, n, len(self.problems), want_fits)
+
+    def kernels_per_sweep(self) -> int:
+        n = ctypes.c_longlong(0)
+        _check(lib().ppl_cpd_batch_kernels(self.b, ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if self.b:

@@ -1164,6 +1164,7 @@ struct ppl_cpd_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool ready;
+    long long kernels;
 };
 
 extern "C" {
@@ -1240,6 +1241,16 @@ int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
         }
         b->graph = gr;
         b->ready = true;
+        size_t nn = 0;
+        cudaGraphGetNodes(gr, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(gr, nodes.data(), &nn);
+        b->kernels = 0;
+        for (size_t q = 0; q < nn; ++q) {
+            cudaGraphNodeType t;
+            cudaGraphNodeGetType(nodes[q], &t);
+            if (t == cudaGraphNodeTypeKernel) ++b->kernels;
+        }
     }
     for (int s = 0; s < nsweeps; ++s) {
         if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess)
@@ -1267,6 +1278,12 @@ int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
     cudaStreamWaitEvent(b->user, b->ev_out, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch: %s", cudaGetErrorString(e));
+    return PPL_OK;
+}
+
+int ppl_cpd_batch_kernels(ppl_cpd_batch* b, long long* kernels_per_sweep) {
+    if (!b || !kernels_per_sweep) return fail(nullptr, PPL_EINVAL, "NULL argument");
+    *kernels_per_sweep = b->ready ? b->kernels : 0;
     return PPL_OK;
 }
 
