@@ -30,7 +30,7 @@ long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
 struct Layout {
     // offsets (bytes) into the workspace; -1 = absent
-    size_t G[4], V, Linv, Z, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
+    size_t G[4], V, Linv, Z, Zi, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
     size_t T64, W64, Y64, S64;                       // FP64 form
     size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Za, Zb, gov, Gblk, Rblk;
@@ -87,6 +87,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.V = take(RR * d);
     L.Linv = take((size_t)((R + 31) / 32) * 32 * 32 * d);
     L.Z = take((size_t)dim * R * d);
+    L.Zi = take(RR * d);
     L.M = take((size_t)dim * R * d);
     L.P = take((size_t)o * o * R * d);
     L.scal = take(NSCAL * d);
@@ -280,7 +281,8 @@ int solve_mode(ppl_cpd* h, int m) {
         if (q != m) oth[k++] = q;
     char* f = h->ws + h->L.flags;
     const int r = solve_mode_coop(h->G(oth[0]), h->G(oth[1]), h->G(oth[2]), h->at<double>(h->L.M), dim, R,
-                                  h->at<double>(h->L.V), h->at<double>(h->L.Linv), h->at<double>(h->L.Z), h->U[m],
+                                  h->at<double>(h->L.V), h->at<double>(h->L.Linv), h->at<double>(h->L.Z),
+                                  h->at<double>(h->L.Zi), h->U[m],
                                   h->lam, h->G(m), reinterpret_cast<unsigned int*>(f + 16),
                                   reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(), h->st);
     if (r != 0)

@@ -3,12 +3,13 @@
 // three Gram matrices, a Cholesky solve of the normal equations, column
 // normalisation; then the new factor's Gram matrix for the next updates).
 //
-//   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, tol = max(2^-52 R max V_kk, 1e-300)
+//   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, Zi = I, tol = max(2^-52 R max V_kk, 1e-300)
 //   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol)
-//       with the rows of Z appended below V, so the same panel and trailing
-//       updates carry out the forward substitution Z <- M L^-T
-//   P2  backward substitution Z <- Z L^-1, block column by block column
-//   P3  lam_r = ||Z[:, r]||, U = Z / lam (a zero column keeps lam = 0)
+//       with the rows of Z and of Zi appended below V, so the same panel and
+//       trailing updates carry out the forward substitutions Z <- M L^-T and
+//       Zi <- L^-T (only the block rows of Zi that are already non-zero are updated)
+//   P2  U~ = Z L^-1 = Z Zi^T as one product over 16 x 16 output tiles
+//   P3  lam_r = ||U~[:, r]||, U = U~ / lam (a zero column keeps lam = 0)
 //   P4  G = U^T U
 //
 // GB300 executes about two FP64 FMAs per clock per SM, so every phase is
@@ -34,6 +35,7 @@ struct SolveP {
     double* Linv;
     const double* M;
     double* Z;
+    double* Zi;
     double* U;
     double* lam;
     double* G;
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         if (q <= r && !(r < kb0 && q < kb0)) p.V[e] = p.G1[e] * p.G2[e] * p.G3[e];
     }
     for (long long e = gtid; e < (long long)dim * R; e += gthreads) p.Z[e] = p.M[e];
+    for (long long e = gtid; e < (long long)R * R; e += gthreads) p.Zi[e] = (e / R == e % R) ? 1.0 : 0.0;
     if (blockIdx.x == 0) {
         // the first diagonal block straight from the Gram matrices
         for (int e = tid; e < kb0 * kb0; e += NT) {
@@ -297,12 +300,17 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         __syncthreads();
         // panel: rows below the block (V) and all rows of Z, 8 rows per task
         const int vrows = R - k0 - kb;
-        const int prow = vrows + dim;
+        const int prow = vrows + dim + k0 + kb;      // V rows below the block, Z rows, Zi rows of blocks <= k
         const int ntask = (prow + 7) / 8;
         for (int task = blockIdx.x; task < ntask; task += G) {
             const int rr = task * 8 + tid / NB, t = tid % NB;
             double* row = nullptr;
-            if (rr < prow) row = (rr < vrows) ? p.V + (long long)(k0 + kb + rr) * R + k0 : p.Z + (long long)(rr - vrows) * R + k0;
+            if (rr < vrows)
+                row = p.V + (long long)(k0 + kb + rr) * R + k0;
+            else if (rr < vrows + dim)
+                row = p.Z + (long long)(rr - vrows) * R + k0;
+            else if (rr < prow)
+                row = p.Zi + (long long)(rr - vrows - dim) * R + k0;
             Ta[tid / NB][t] = (row && t < kb) ? __ldcg(row + t) : 0.0;
             __syncthreads();
             if (row && t < kb) {
@@ -318,7 +326,8 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         // blocks take the remaining tiles.
         const int Tk = (vrows + NB - 1) / NB;
         const int ntri = Tk * (Tk + 1) / 2;
-        const int ntile = ntri + D * Tk;
+        const int nz = ntri + D * Tk;
+        const int ntile = nz + (k + 1) * Tk;
         int first, stride;
         if (G == 1) {
             first = 0;
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 Pa = p.V + (long long)i0 * R + k0;
                 arows = R - i0;
                 C = p.V + (long long)i0 * R + j0;
-            } else {
+            } else if (tile < nz) {
                 const int tz = tile - ntri;
                 const int Mb = tz / Tk, J = tz % Tk;
                 i0 = Mb * NB;
@@ -351,6 +360,14 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 Pa = p.Z + (long long)i0 * R + k0;
                 arows = dim - i0;
                 C = p.Z + (long long)i0 * R + j0;
+            } else {
+                const int tz = tile - nz;
+                const int Ib = tz / Tk, J = tz % Tk;
+                i0 = Ib * NB;
+                j0 = k0 + kb + J * NB;
+                Pa = p.Zi + (long long)i0 * R + k0;
+                arows = min(NB, k0 + kb - i0);
+                C = p.Zi + (long long)i0 * R + j0;
             }
             const int brows = R - j0;
             const double* Pb = p.V + (long long)j0 * R + k0;
@@ -385,110 +402,72 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         if (!gsync(p, gen, &s_flag)) return;
     }
 
-    // ---- P2: backward substitution Z <- Z L^-1 -------------------------------------
-    for (int k = nt - 1; k >= 0; --k) {
-        const int k0 = k * NB, kb = min(NB, R - k0);
-        for (int e = tid; e < NB * NB; e += NT) Li[e / NB][e % NB] = __ldcg(p.Linv + (long long)k * NB * NB + e);
-        __syncthreads();
-        const int ntask = (dim + 7) / 8;
-        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
-            const int rr = task * 8 + tid / NB, t = tid % NB;
-            double* row = (rr < dim) ? p.Z + (long long)rr * R + k0 : nullptr;
-            Ta[tid / NB][t] = (row && t < kb) ? __ldcg(row + t) : 0.0;
-            __syncthreads();
-            if (row && t < kb) {
-                double s = 0.0;
-                for (int q = t; q < kb; ++q) s = fma(Ta[tid / NB][q], Li[q][t], s);
-                row[t] = s;
-            }
-            __syncthreads();
-        }
-        if (!gsync(p, gen, &s_flag)) return;
-        if (k > 0) {
-            const int ntile = D * k;
-            for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-                const int Mb = tile / k, J = tile % k;
-                const int i0 = Mb * NB, j0 = J * NB;
-                const int arows = dim - i0;
-                for (int e = tid; e < NB * NB; e += NT) {
-                    const int i = e / NB, s = e % NB;
-                    Ta[i][s] = (i < arows && s < kb) ? __ldcg(p.Z + (long long)(i0 + i) * R + k0 + s) : 0.0;
-                    Tb[i][s] = (i < kb) ? __ldcg(p.V + (long long)(k0 + i) * R + j0 + s) : 0.0;   // Tb[t][j] = L[k0+t][j0+j]
+    // ---- P2: U~ = Z L^-1 = Z Zi^T over 16 x 16 tiles, longest rows of Zi first ------
+    constexpr int T16 = 16;
+    const int ty16 = tid / T16, tx16 = tid % T16;
+    {
+        const int D16 = (dim + T16 - 1) / T16, C16 = (R + T16 - 1) / T16;
+        const int ntile = D16 * C16;
+        for (int tile = blockIdx.x; tile < ntile; tile += G) {
+            const int cb = tile / D16, xb = tile % D16;
+            const int x0 = xb * T16, c0 = cb * T16;
+            double acc = 0.0;
+            for (int s0 = c0; s0 < R; s0 += NB) {     // Zi[c][s] = 0 for s < c
+                for (int e = tid; e < T16 * NB; e += NT) {
+                    const int i = e / NB, j = e % NB;
+                    const bool oks = (s0 + j < R);
+                    Ta[i][j] = (oks && x0 + i < dim) ? __ldcg(p.Z + (long long)(x0 + i) * R + s0 + j) : 0.0;
+                    Tb[i][j] = (oks && c0 + i < R) ? __ldcg(p.Zi + (long long)(c0 + i) * R + s0 + j) : 0.0;
                 }
                 __syncthreads();
-                double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
-                for (int s = 0; s < kb; ++s) {
-                    const double x0 = Ta[ty][s], x1 = Ta[ty + 16][s];
-                    const double y0 = Tb[s][tx], y1 = Tb[s][tx + 16];
-                    a00 = fma(x0, y0, a00);
-                    a01 = fma(x0, y1, a01);
-                    a10 = fma(x1, y0, a10);
-                    a11 = fma(x1, y1, a11);
-                }
-                const double acc[2][2] = {{a00, a01}, {a10, a11}};
-                for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b) {
-                        const int i = ty + 16 * a, j = tx + 16 * b;
-                        if (i < arows) {
-                            double* c = p.Z + (long long)(i0 + i) * R + j0 + j;
-                            *c = __ldcg(c) - acc[a][b];
-                        }
-                    }
+#pragma unroll 8
+                for (int j = 0; j < NB; ++j) acc = fma(Ta[ty16][j], Tb[tx16][j], acc);
                 __syncthreads();
             }
+            if (x0 + ty16 < dim && c0 + tx16 < R) p.U[(long long)(x0 + ty16) * R + c0 + tx16] = acc;
         }
-        if (!gsync(p, gen, &s_flag)) return;
     }
+    if (!gsync(p, gen, &s_flag)) return;
 
     // ---- P3: normalise -------------------------------------------------------------
     for (long long r = gtid; r < R; r += gthreads) {
         double s = 0.0;
         for (int x = 0; x < dim; ++x) {
-            const double u = __ldcg(p.Z + (long long)x * R + r);
+            const double u = __ldcg(p.U + (long long)x * R + r);
             s = fma(u, u, s);
         }
         const double l = sqrt(s);
         const double inv = (l > 0.0) ? 1.0 / l : 1.0;
-        for (int x = 0; x < dim; ++x) p.U[(long long)x * R + r] = __ldcg(p.Z + (long long)x * R + r) * inv;
+        for (int x = 0; x < dim; ++x) p.U[(long long)x * R + r] = __ldcg(p.U + (long long)x * R + r) * inv;
         p.lam[r] = l;
     }
     if (!gsync(p, gen, &s_flag)) return;
 
-    // ---- P4: Gram of the new factor -------------------------------------------------
-    const int TR = (R + NB - 1) / NB;
+    // ---- P4: Gram of the new factor, 16 x 16 tiles of the lower triangle ------------
+    const int TR = (R + T16 - 1) / T16;
     const int ntri = TR * (TR + 1) / 2;
-    for (int tile = blockIdx.x; tile < ntri; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntri; tile += G) {
         int I, J;
         tri_index(tile, I, J);
-        const int i0 = I * NB, j0 = J * NB;
-        double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+        const int i0 = I * T16, j0 = J * T16;
+        double acc = 0.0;
         for (int x0 = 0; x0 < dim; x0 += NB) {
-            for (int e = tid; e < NB * NB; e += NT) {
-                const int x = e / NB, c = e % NB;
+            for (int e = tid; e < NB * T16; e += NT) {
+                const int x = e / T16, c = e % T16;
                 const bool okx = (x0 + x < dim);
                 Ta[x][c] = (okx && i0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + i0 + c) : 0.0;
                 Tb[x][c] = (okx && j0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + j0 + c) : 0.0;
             }
             __syncthreads();
-            for (int x = 0; x < NB; ++x) {
-                const double u0 = Ta[x][ty], u1 = Ta[x][ty + 16];
-                const double w0 = Tb[x][tx], w1 = Tb[x][tx + 16];
-                a00 = fma(u0, w0, a00);
-                a01 = fma(u0, w1, a01);
-                a10 = fma(u1, w0, a10);
-                a11 = fma(u1, w1, a11);
-            }
+#pragma unroll 8
+            for (int x = 0; x < NB; ++x) acc = fma(Ta[x][ty16], Tb[x][tx16], acc);
             __syncthreads();
         }
-        const double acc[2][2] = {{a00, a01}, {a10, a11}};
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-                const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
-                if (i < R && j < R) {
-                    p.G[(long long)i * R + j] = acc[a][b];
-                    p.G[(long long)j * R + i] = acc[a][b];
-                }
-            }
+        const int i = i0 + ty16, j = j0 + tx16;
+        if (i < R && j < R) {
+            p.G[(long long)i * R + j] = acc;
+            p.G[(long long)j * R + i] = acc;
+        }
     }
 }
 
@@ -497,8 +476,9 @@ int g_solve_grid = 0;
 }  // namespace
 
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
-                    double* V, double* Linv, double* Z, double* U, double* lam, double* G, unsigned int* sync,
-                    unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err, cudaStream_t s) {
+                    double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
+                    unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
+                    cudaStream_t s) {
     if (g_solve_grid == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
@@ -511,15 +491,16 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
     // panel rows), so that several instances' solves can share the GPU
     const int t0 = (R > NB) ? (R - NB + NB - 1) / NB : 0;
     const int d = (dim + NB - 1) / NB;
-    int want = t0 * (t0 + 1) / 2 + d * t0;
-    const int ptask = (R - (R < NB ? R : NB) + dim + 7) / 8;
+    int want = t0 * (t0 + 1) / 2 + d * t0 + t0;
+    const int ptask = (R + dim + 7) / 8;
     if (ptask > want) want = ptask;
     if (want < 8) want = 8;
     const int grid = want < g_solve_grid ? want : g_solve_grid;
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
     SolveP p;
-    p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.U = U; p.lam = lam; p.G = G;
+    p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.Zi = Zi; p.U = U; p.lam = lam;
+    p.G = G;
     p.sync = sync; p.maxdiag = maxdiag; p.nclamp = nclamp; p.err = err; p.R = R; p.dim = dim;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
