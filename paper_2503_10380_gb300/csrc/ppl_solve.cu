@@ -54,20 +54,32 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 __device__ __forceinline__ unsigned int ld_vol(const unsigned int* p) { return *(volatile const unsigned int*)p; }
 
-// grid-wide barrier; false when the wait expired or another block aborted
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// grid-wide barrier; false when the wait expired or another block aborted.
+// The block's writes are ordered before its arrival by __syncthreads and the
+// release of the arrival; the waiters' acquire loads order what follows.
 __device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&p.sync[0], 1u) + 1u;
+        const unsigned int arrived = atom_add_release(&p.sync[0], 1u) + 1u;
         if (arrived == gridDim.x) {
             atomicExch(&p.sync[0], 0u);
-            __threadfence();
-            atomicAdd(&p.sync[1], 1u);
+            atom_add_release(&p.sync[1], 1u);
         } else {
             const unsigned long long t0 = gtimer();
-            while (ld_vol(&p.sync[1]) == gen) {
+            while (ld_acquire(&p.sync[1]) == gen) {
                 if (ld_vol(&p.sync[2])) {
                     ok = 0;
                     break;
@@ -80,7 +92,6 @@ __device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
                 }
             }
         }
-        __threadfence();
         gen += 1;
         if (ld_vol(&p.sync[2])) ok = 0;
         *s_flag = ok;
@@ -226,7 +237,6 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
         if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
     }
     for (int e = tid; e < NB * NB; e += NT) p.Linv[(long long)k * NB * NB + e] = Li[e / NB][e % NB];
-    __threadfence();
     __syncthreads();
 }
 
@@ -282,7 +292,6 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 p.V[d] = p.G1[d] * p.G2[d] * p.G3[d];
             }
         }
-        __threadfence();
         __syncthreads();
         factor_block(p, 0, tol, Ls, Li, rd, tri, Tb);
     }
@@ -395,7 +404,6 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                         *c = __ldcg(c) - acc[a][b];
                     }
                 }
-            __threadfence();
             __syncthreads();
             if (tile == 0 && k + 1 < nt) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
         }
@@ -429,17 +437,33 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     }
     if (!gsync(p, gen, &s_flag)) return;
 
-    // ---- P3: normalise -------------------------------------------------------------
-    for (long long r = gtid; r < R; r += gthreads) {
-        double s = 0.0;
-        for (int x = 0; x < dim; ++x) {
-            const double u = __ldcg(p.U + (long long)x * R + r);
-            s = fma(u, u, s);
+    // ---- P3: normalise: 32 columns per block, 8 row groups, a zero column keeps lam = 0
+    {
+        const int c = tid % 32, rg = tid / 32;
+        for (int cb = blockIdx.x; cb * 32 < R; cb += G) {
+            const int r = cb * 32 + c;
+            double s = 0.0;
+            if (r < R)
+                for (int x = rg; x < dim; x += NT / 32) {
+                    const double u = __ldcg(p.U + (long long)x * R + r);
+                    s = fma(u, u, s);
+                }
+            Ta[rg][c] = s;
+            __syncthreads();
+            if (rg == 0) {
+                double t = 0.0;
+                for (int q = 0; q < NT / 32; ++q) t += Ta[q][c];
+                Tb[0][c] = t;
+            }
+            __syncthreads();
+            if (r < R) {
+                const double l = sqrt(Tb[0][c]);
+                const double inv = (l > 0.0) ? 1.0 / l : 1.0;
+                for (int x = rg; x < dim; x += NT / 32) p.U[(long long)x * R + r] = __ldcg(p.U + (long long)x * R + r) * inv;
+                if (rg == 0) p.lam[r] = l;
+            }
+            __syncthreads();
         }
-        const double l = sqrt(s);
-        const double inv = (l > 0.0) ? 1.0 / l : 1.0;
-        for (int x = 0; x < dim; ++x) p.U[(long long)x * R + r] = __ldcg(p.U + (long long)x * R + r) * inv;
-        p.lam[r] = l;
     }
     if (!gsync(p, gen, &s_flag)) return;
 
