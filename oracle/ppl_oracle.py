@@ -58,9 +58,20 @@ MODES = ("a", "b", "i", "j")
 # explicit tensors (tiny sizes only)
 # --------------------------------------------------------------------------
 
-def ppl_tensor(Bvv: np.ndarray, tau: np.ndarray) -> np.ndarray:
-    """R[a,b,i,j] = sum_cd (sum_Q B[Q,a,c] B[Q,b,d]) tau[i,j,c,d]; Eq. (dfB) with D-bar = D."""
-    G = np.einsum("Qac,Qbd->abcd", Bvv, Bvv)
+def dress(B: np.ndarray, t1: np.ndarray, o: int) -> np.ndarray:
+    """D-bar^{bX}_d = D^{bX}_d - 2 sum_k D^{bX}_k t^k_d, the intermediate defined after
+    Eq. (fulldfB) (its X index, missing in the printed definition, restored).
+    B [X][o+v][o+v], t1 [o][v] (t^a_i as t1[i, a]).  Returns D-bar over (Q, b, d) = [X][v][v]."""
+    Bvv = B[:, o:, o:]
+    Bvo = B[:, o:, :o]
+    return Bvv - 2.0 * np.einsum("Qbk,kd->Qbd", Bvo, t1)
+
+
+def ppl_tensor(Bvv: np.ndarray, tau: np.ndarray, Bbar: np.ndarray | None = None) -> np.ndarray:
+    """R[a,b,i,j] = sum_cd (sum_Q B[Q,a,c] Bbar[Q,b,d]) tau[i,j,c,d]; Eq. (dfB), with
+    Bbar = B unless a dressed D-bar is given."""
+    Bb = Bvv if Bbar is None else Bbar
+    G = np.einsum("Qac,Qbd->abcd", Bvv, Bb)
     return np.einsum("abcd,ijcd->abij", G, tau)
 
 
@@ -144,12 +155,12 @@ def mttkrp_b(Bvv, T, Da):
     return M
 
 
-def p_intermediate(Bvv, tau, Ua, Ub):
+def p_intermediate(Bvv, tau, Ua, Ub, Bbar=None):
     """For modes i and j: S_r[c, d] = sum_Q Da[r,Q,c] Db[r,Q,d] and
-    P[i, j, r] = sum_cd tau[i,j,c,d] S_r[c,d]."""
+    P[i, j, r] = sum_cd tau[i,j,c,d] S_r[c,d]; Db from D-bar when dressed."""
     o, _, v, _ = tau.shape
     Da = dbar_r(Bvv, Ua)
-    Db = dbar_r(Bvv, Ub)
+    Db = dbar_r(Bvv if Bbar is None else Bbar, Ub)
     R = Ua.shape[1]
     S = np.empty((R, v, v))
     for r in range(R):
@@ -158,13 +169,15 @@ def p_intermediate(Bvv, tau, Ua, Ub):
     return P.reshape(o, o, R)
 
 
-def mttkrp(Bvv: np.ndarray, tau: np.ndarray, U: dict, mode: str) -> np.ndarray:
-    """Matrix-free MTTKRP of R (never formed) for one mode; result [dim, R]."""
+def mttkrp(Bvv: np.ndarray, tau: np.ndarray, U: dict, mode: str, Bbar=None) -> np.ndarray:
+    """Matrix-free MTTKRP of R (never formed) for one mode; result [dim, R].  With a
+    dressed D-bar, the b side (second factor of Eq. dfB) uses it."""
+    Bb = Bvv if Bbar is None else Bbar
     if mode == "a":
-        return mttkrp_a(Bvv, tau_r(tau, U["i"], U["j"]), dbar_r(Bvv, U["b"]))
+        return mttkrp_a(Bvv, tau_r(tau, U["i"], U["j"]), dbar_r(Bb, U["b"]))
     if mode == "b":
-        return mttkrp_b(Bvv, tau_r(tau, U["i"], U["j"]), dbar_r(Bvv, U["a"]))
-    P = p_intermediate(Bvv, tau, U["a"], U["b"])
+        return mttkrp_b(Bb, tau_r(tau, U["i"], U["j"]), dbar_r(Bvv, U["a"]))
+    P = p_intermediate(Bvv, tau, U["a"], U["b"], Bbar)
     if mode == "i":
         return np.einsum("ijr,jr->ir", P, U["j"])
     if mode == "j":
@@ -270,22 +283,25 @@ def fit_value(normR2: float, inner: float, norm2: float) -> float:
 # ALS
 # --------------------------------------------------------------------------
 
-def als_sweep(Bvv, tau, U: dict, lam: np.ndarray, normR2: float | None = None):
+def als_sweep(Bvv, tau, U: dict, lam: np.ndarray, normR2: float | None = None, Bbar=None):
     """One ALS sweep a -> b -> i -> j.  tau_r is shared by modes a and b and
     P by modes i and j (the cached intermediates of the paper).  Returns
     (U, lam, info) with info = dict(inner, norm2, fit, nclamped, M)."""
     U = {m: U[m].copy() for m in MODES}
+    Bb = Bvv if Bbar is None else Bbar
     nclamp = 0
     Ms = {}
     T = tau_r(tau, U["i"], U["j"])
     for mode in ("a", "b"):
-        other = dbar_r(Bvv, U["b"] if mode == "a" else U["a"])
-        M = mttkrp_a(Bvv, T, other) if mode == "a" else mttkrp_b(Bvv, T, other)
+        if mode == "a":
+            M = mttkrp_a(Bvv, T, dbar_r(Bb, U["b"]))
+        else:
+            M = mttkrp_b(Bb, T, dbar_r(Bvv, U["a"]))
         Ut, nc = solve_normal(M, hadamard_v(U, mode))
         U[mode], lam = normalise(Ut)
         Ms[mode] = M
         nclamp += nc
-    P = p_intermediate(Bvv, tau, U["a"], U["b"])
+    P = p_intermediate(Bvv, tau, U["a"], U["b"], Bbar)
     for mode in ("i", "j"):
         if mode == "i":
             M = np.einsum("ijr,jr->ir", P, U["j"])
@@ -301,14 +317,14 @@ def als_sweep(Bvv, tau, U: dict, lam: np.ndarray, normR2: float | None = None):
     return U, lam, dict(inner=inner, norm2=norm2, fit=fit, nclamped=nclamp, M=Ms)
 
 
-def cp_als(Bvv, tau, U0: dict, nsweeps: int, normR2: float | None = None, lam0=None):
+def cp_als(Bvv, tau, U0: dict, nsweeps: int, normR2: float | None = None, lam0=None, Bbar=None):
     """nsweeps ALS sweeps from the initial factors U0 (lam starts at ones).
     Returns (U, lam, history) with one info dict per sweep (plus eta)."""
     U = {m: np.array(U0[m], dtype=np.float64, copy=True) for m in MODES}
     lam = np.ones(U["a"].shape[1]) if lam0 is None else np.array(lam0, dtype=np.float64)
     hist = []
     for _ in range(nsweeps):
-        Un, lamn, info = als_sweep(Bvv, tau, U, lam, normR2)
+        Un, lamn, info = als_sweep(Bvv, tau, U, lam, normR2, Bbar)
         info["eta"] = eta(Un, lamn, U, lam)
         hist.append(info)
         U, lam = Un, lamn
@@ -345,16 +361,17 @@ def energy_cp(B: np.ndarray, o: int, U: dict, lam: np.ndarray) -> float:
     return float(np.sum(lam * np.sum(t, axis=0)))
 
 
-def exact_rows(B: np.ndarray, tau: np.ndarray, o: int, a_rows) -> tuple:
+def exact_rows(B: np.ndarray, tau: np.ndarray, o: int, a_rows, Bbar=None) -> tuple:
     """Rows R[a, :, :, :] of the exact tensor for the given a, with their
     contributions to ||R||^2 and to E.  Returns (R_rows [len, v, o, o], norm2_part, E_part)."""
     Bvv = B[:, o:, o:]
+    Bb = Bvv if Bbar is None else Bbar
     Bov = B[:, :o, o:]
     v = Bvv.shape[1]
     tau2 = tau.reshape(o * o, v * v)
     rows, n2, E = [], 0.0, 0.0
     for a in a_rows:
-        Ga = np.tensordot(Bvv[:, a, :], Bvv, axes=([0], [0]))        # [c, b, d]
+        Ga = np.tensordot(Bvv[:, a, :], Bb, axes=([0], [0]))         # [c, b, d]
         Ra = (Ga.transpose(1, 0, 2).reshape(v, v * v) @ tau2.T).reshape(v, o, o)   # [b, i, j]
         # 2 g[i a j b] - g[i b j a]
         g1 = np.einsum("Qi,Qjb->bij", Bov[:, :, a], Bov)
@@ -365,10 +382,10 @@ def exact_rows(B: np.ndarray, tau: np.ndarray, o: int, a_rows) -> tuple:
     return np.stack(rows) if rows else np.zeros((0, v, o, o)), n2, E
 
 
-def exact_contract(B: np.ndarray, tau: np.ndarray, o: int):
+def exact_contract(B: np.ndarray, tau: np.ndarray, o: int, Bbar=None):
     """||R||^2 and E_exact over all rows a."""
     v = B.shape[1] - o
-    _, n2, E = exact_rows(B, tau, o, range(v))
+    _, n2, E = exact_rows(B, tau, o, range(v), Bbar)
     return n2, E
 
 

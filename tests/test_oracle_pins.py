@@ -357,3 +357,52 @@ def test_torch_generator_matches_numpy_generator():
     assert np.max(np.abs(tau.numpy() - a.tau)) < 1e-12 * np.max(np.abs(a.tau))
     for m in orc.MODES:
         assert np.array_equal(f[m], a.factors[m])
+
+
+
+# ---------------------------------------------------------------- t1-dressed D-bar
+
+def test_dressed_tensor_is_the_two_term_fulldfB_by_loops():
+    """Eq. (fulldfB) written out term by term with loops equals R built from dress()."""
+    inp = inputs.make_inputs(o=2, v=3, X=2, R=2, seed=17)
+    o, v, X = 2, 3, 2
+    B, t1, tau = inp.B, inp.t1, inp.tau
+    R = np.zeros((v, v, o, o))
+    for a, b, i, j in itertools.product(range(v), range(v), range(o), range(o)):
+        s = 0.0
+        for c, d, Q in itertools.product(range(v), range(v), range(X)):
+            term = B[Q, o + a, o + c] * B[Q, o + b, o + d]
+            for k in range(o):
+                term -= 2.0 * B[Q, o + a, o + c] * B[Q, o + b, k] * t1[k, d]
+            s += term * tau[i, j, c, d]
+        R[a, b, i, j] = s
+    Bbar = orc.dress(B, t1, o)
+    assert _rel(orc.ppl_tensor(inp.Bvv, tau, Bbar), R) < 1e-13
+
+
+@pytest.mark.parametrize("mode", orc.MODES)
+def test_dressed_matrix_free_mttkrp_equals_explicit(tiny, mode):
+    Bbar = orc.dress(tiny.B, tiny.t1, tiny.o)
+    Rt = orc.ppl_tensor(tiny.Bvv, tiny.tau, Bbar)
+    assert _rel(orc.mttkrp(tiny.Bvv, tiny.tau, tiny.factors, mode, Bbar),
+                orc.mttkrp_explicit(Rt, tiny.factors, mode)) < 1e-12
+
+
+def test_dressing_moves_the_pair_symmetry_to_swapped_factors(tiny):
+    Bbar = orc.dress(tiny.B, tiny.t1, tiny.o)
+    R1 = orc.ppl_tensor(tiny.Bvv, tiny.tau, Bbar)          # sum B(a) Bbar(b) tau
+    assert _rel(R1, R1.transpose(1, 0, 3, 2)) > 1e-3       # no longer pair symmetric
+    G2 = np.einsum("Qac,Qbd->abcd", Bbar, tiny.Bvv)          # the dressing on the a side
+    R2 = np.einsum("abcd,ijcd->abij", G2, tiny.tau)
+    assert _rel(R1, R2.transpose(1, 0, 3, 2)) < 1e-13
+
+
+def test_dressed_exact_rows_and_sweep(tiny):
+    Bbar = orc.dress(tiny.B, tiny.t1, tiny.o)
+    Rt = orc.ppl_tensor(tiny.Bvv, tiny.tau, Bbar)
+    n2, E = orc.exact_contract(tiny.B, tiny.tau, tiny.o, Bbar)
+    assert abs(n2 - float(np.sum(Rt * Rt))) < 1e-12 * n2
+    assert abs(E - orc.energy_of_tensor(Rt, tiny.B, tiny.o)) < 1e-12 * abs(E)
+    U1, lam1, info = orc.als_sweep(tiny.Bvv, tiny.tau, tiny.factors, np.ones(tiny.R), n2, Bbar)
+    fit = 1 - np.linalg.norm(Rt - orc.reconstruct(U1, lam1)) / np.linalg.norm(Rt)
+    assert abs(info["fit"] - fit) < 1e-10
