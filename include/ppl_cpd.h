@@ -63,7 +63,8 @@ typedef struct {
     int use_graph;   /* 1: capture one sweep in a CUDA graph on first use and replay it  */
     int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
     int profile;     /* 1: record CUDA events between the phases of every sweep           */
-    int reserved[11];
+    int dressed;     /* 1: reserve room for the t1-dressed D-bar (ppl_cpd_set_t1)         */
+    int reserved[10];
 } ppl_cpd_opts;
 
 typedef struct {
@@ -136,6 +137,14 @@ int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_ou
  * replaced by 0.5 (R~[a,b,i,j] + R~[b,a,j,i]), the post-reconstruction
  * symmetrisation of the CPD-PPL section.  2 v^2 o^2 R flops, FP64. */
 int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise);
+
+/* Use the t1-dressed D-bar of Eq. fulldfB on the b side of the PPL tensor,
+ *   D-bar[Q,b,d] = B[Q,b,d] - 2 sum_k B[Q,b,k] t1[k,d]  (k occupied, b, d virtual),
+ *   R[a,b,i,j]  = sum_{Q,c,d} B[Q,a,c] D-bar[Q,b,d] tau[i,j,c,d].
+ * t1 [o][v] FP64 device (t1[i][a] = t^a_i); NULL restores D-bar = B.  Needs
+ * opts.dressed = 1 at ppl_cpd_init (EINVAL otherwise).  The stored ||R||^2 is
+ * forgotten.  Energies keep g from the undressed B. */
+int ppl_cpd_set_t1(ppl_cpd* h, const double* t1);
 
 /* Point the handle at a new tau (same shape, device) for the next CC-like
  * step; the factors in the caller's buffer are kept as the warm start

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4
 
 class ppl_cpd_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
-                ("profile", c_int), ("reserved", c_int * 11)]
+                ("profile", c_int), ("dressed", c_int), ("reserved", c_int * 10)]
 
 
 class ppl_cpd_stats(ctypes.Structure):
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_factors_changed.argtypes = [H]
     L.ppl_cpd_set_guess_policy.argtypes = [H, c_int]
     L.ppl_cpd_reconstruct.argtypes = [H, c_void_p, c_int]
+    L.ppl_cpd_set_t1.argtypes = [H, c_void_p]
     L.ppl_cpd_autotune.argtypes = [H, POINTER(c_int)]
     L.ppl_cpd_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int, c_void_p]
     L.ppl_cpd_batch_sweep.argtypes = [c_void_p, c_int, POINTER(c_double)]
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
                  "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct", "ppl_cpd_autotune",
+                 "ppl_cpd_set_t1",
                  "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy", "ppl_cpd_batch_kernels",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
@@ -102,7 +104,8 @@ def _check(rc: int, h=None):
         raise PplError(rc, msg.decode() if msg else "")
 
 
-def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, profile=False) -> ppl_cpd_opts:
+def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
+              dressed=False) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -110,6 +113,7 @@ def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, pro
     o.use_graph = int(bool(use_graph))
     o.want_eta = int(bool(want_eta))
     o.profile = int(bool(profile))
+    o.dressed = int(bool(dressed))
     return o
 
 
@@ -166,6 +170,10 @@ def ppl_cpd_set_tau(h, tau_ptr):
 
 def ppl_cpd_factors_changed(h):
     _check(lib().ppl_cpd_factors_changed(h), h)
+
+
+def ppl_cpd_set_t1(h, t1_ptr):
+    _check(lib().ppl_cpd_set_t1(h, t1_ptr), h)
 
 
 def ppl_cpd_reconstruct(h, R_ptr, symmetrise: bool):
@@ -288,7 +296,7 @@ class CpAls:
     """
 
     def __init__(self, B, tau, factors, precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False,
-                 profile=False, stream=None):
+                 profile=False, dressed=False, stream=None):
         import torch
         self.torch = torch
         X, n, _ = B.shape
@@ -303,7 +311,7 @@ class CpAls:
         parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
         parts.append(torch.ones(R, dtype=torch.float64))
         self.fac = torch.cat(parts).to(dev)
-        self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile)
+        self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile, dressed)
         self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -344,6 +352,11 @@ class CpAls:
             Rt = self.torch.empty((self.v, self.v, self.o, self.o), dtype=self.torch.float64, device=self.B.device)
         n2, E = ppl_exact_contract(self.h, Rt.data_ptr() if Rt is not None else None)
         return n2, E, Rt
+
+    def set_t1(self, t1):
+        """Dress the b side with t1 [o][v] (FP64 device tensor), or undress with None."""
+        self.t1 = None if t1 is None else t1.contiguous()
+        ppl_cpd_set_t1(self.h, None if self.t1 is None else self.t1.data_ptr())
 
     def set_tau(self, tau):
         self.tau = tau.contiguous()

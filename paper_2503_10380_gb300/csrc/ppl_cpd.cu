@@ -33,6 +33,7 @@ struct Layout {
     size_t G[4], V, Linv, Z, Zi, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
     size_t T64, W64, Y64, S64;                       // FP64 form
     size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
+    size_t Bbar, BbN, BbP, BbT;   // t1-dressed D-bar: FP64 [X][v][v] and its operand layouts
     size_t Za, Zb, gov, Gblk, Rblk;
     size_t ring, cache, guess0;   // 6 iterates, the Near-Optimal cache, the initial guess
     size_t recon;                 // Khatri-Rao chunks for the reconstruction
@@ -113,6 +114,8 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.T64 = L.W64 = L.Y64 = L.S64 = none;
     L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
     L.PART = none;
+    L.Bbar = L.BbN = L.BbP = L.BbT = none;
+    if (op.dressed) L.Bbar = take((size_t)X * v * v * d);
     if (!tc) {
         L.T64 = take((size_t)R * v * v * d);
         L.W64 = take((size_t)rc * X * v * d);
@@ -135,6 +138,11 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.WTb = take((size_t)rc * v * L.ldX * e);
         L.S = take((size_t)rc * L.ldvv * e);
         L.PART = take((size_t)KSMAX * (size_t)(v > o * o ? v : o * o) * rc * sizeof(float));
+        if (op.dressed) {
+            L.BbN = take((size_t)X * v * L.ldv * e);
+            L.BbP = take((size_t)v * X * L.ldv * e);
+            L.BbT = take((size_t)v * X * L.ldv * e);
+        }
     }
     L.total = off;
     return true;
@@ -180,6 +188,7 @@ struct ppl_cpd {
     unsigned int* errflag() const { return reinterpret_cast<unsigned int*>(ws + L.flags + 8); }
     int dim(int m) const { return m < 2 ? v : o; }
     bool tc() const { return opts.precision != PPL_PREC_FP64; }
+    bool dressed() const { return opts.dressed != 0; }
 };
 
 namespace {
@@ -305,11 +314,15 @@ void t_fp64(ppl_cpd* h) {
     gemm64(g, h->st);
 }
 
-// W[r][Q][d] = sum_b B[Q][o+b][o+d] U[b][r0+r]
-void w_fp64(ppl_cpd* h, const double* U, int r0, int rcur, double* W) {
+// W[r][Q][d] = sum_b B[Q][o+b][o+d] U[b][r0+r]; bside: the dressed D-bar[Q][b][d]
+void w_fp64(ppl_cpd* h, const double* U, int r0, int rcur, double* W, bool bside = false) {
     const int o = h->o, v = h->v, X = h->X, R = h->R, n = h->n;
     G64 g{};
-    g.A = h->B + (long long)o * n + o; g.am = ix2(v, (long long)n * n, n); g.ak = ix1(1);
+    if (bside && h->dressed()) {
+        g.A = h->at<double>(h->L.Bbar); g.am = ix2(v, (long long)v * v, 1); g.ak = ix1(v);
+    } else {
+        g.A = h->B + (long long)o * n + o; g.am = ix2(v, (long long)n * n, n); g.ak = ix1(1);
+    }
     g.B = U + r0; g.bn = ix1(1); g.bk = ix1(R);
     g.C = W; g.cm = ix1(1); g.cn = ix1((long long)X * v);
     g.M = X * v; g.N = rcur; g.K = v; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
@@ -324,7 +337,7 @@ void mttkrp_ab_fp64(ppl_cpd* h, int mode, double* Mout) {
     cudaMemsetAsync(Mout, 0, (size_t)v * R * sizeof(double), h->st);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
-        w_fp64(h, mode == 0 ? h->U[1] : h->U[0], r0, rcur, W);
+        w_fp64(h, mode == 0 ? h->U[1] : h->U[0], r0, rcur, W, mode == 0);
         G64 y{};
         y.A = W; y.ab = (long long)X * v; y.am = ix1(v); y.ak = ix1(1);
         y.B = T + (long long)r0 * v * v; y.bb = (long long)v * v;
@@ -334,7 +347,11 @@ void mttkrp_ab_fp64(ppl_cpd* h, int mode, double* Mout) {
         y.M = X; y.N = v; y.K = v; y.batch = rcur; y.ksplit = 1; y.alpha = 1.0;
         gemm64(y, h->st);
         G64 m{};
-        m.A = h->B + (long long)o * n + o; m.am = ix1(n); m.ak = ix2(v, (long long)n * n, 1);
+        if (mode == 1 && h->dressed()) {
+            m.A = h->at<double>(h->L.Bbar); m.am = ix1(v); m.ak = ix2(v, (long long)v * v, 1);
+        } else {
+            m.A = h->B + (long long)o * n + o; m.am = ix1(n); m.ak = ix2(v, (long long)n * n, 1);
+        }
         m.B = Y; m.bn = ix1((long long)X * v); m.bk = ix1(1);
         m.C = Mout + r0; m.cm = ix1(R); m.cn = ix1(1);
         m.M = v; m.N = rcur; m.K = X * v; m.batch = 1; m.alpha = 1.0; m.atomic = 1;
@@ -356,7 +373,7 @@ void p_fp64(ppl_cpd* h) {
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
         w_fp64(h, h->U[0], r0, rcur, Wa);
-        w_fp64(h, h->U[1], r0, rcur, Wb);
+        w_fp64(h, h->U[1], r0, rcur, Wb, true);
         G64 s{};
         s.A = Wa; s.ab = (long long)X * v; s.am = ix1(1); s.ak = ix1(v);
         s.B = Wb; s.bb = (long long)X * v; s.bn = ix1(1); s.bk = ix1(v);
@@ -451,7 +468,7 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
         // W[r][Q][d] = sum_b B[Q][d][b] U[b][r0+r]
         TcGemm g1{};
-        g1.A = mat(opb(h, h->L.Bn), pB, X * v, v, 1, ldv, 0);
+        g1.A = mat(opb(h, (mode == 0 && h->dressed()) ? h->L.BbN : h->L.Bn), pB, X * v, v, 1, ldv, 0);
         g1.B = mat(opb(h, h->L.UopA), pU, R, v, 1, ldv, 0);
         g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
         g1.out = out_split(opb(h, h->L.W), pW, 0, v, ldv, 1, 0, 0, (long long)X * ldv);
@@ -469,7 +486,7 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
         if (e) return e;
         // M[a][r0+r] += sum_{Q,c} B[Q][a][c] Y[r][Q][c]
         TcGemm g3{};
-        g3.A = mat(opb(h, h->L.Bp), pB, v, (int)(X * ldv), 1, X * ldv, 0);
+        g3.A = mat(opb(h, (mode == 1 && h->dressed()) ? h->L.BbP : h->L.Bp), pB, v, (int)(X * ldv), 1, X * ldv, 0);
         g3.B = mat(opb(h, h->L.Y), pW, rc, (int)(X * ldv), 1, X * ldv, 0);
         g3.M = v; g3.N = rcur; g3.K = (int)(X * ldv); g3.batch = 1;
         e = run_tc_partial(h, g3, Mout + r0, R, "M");
@@ -493,7 +510,7 @@ int p_tc(ppl_cpd* h) {
         for (int w = 0; w < 2; ++w) {
             // WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; rows (c,Q) of Bp
             TcGemm g1{};
-            g1.A = mat(opb(h, h->L.Bp), pB, v * X, v, 1, ldv, 0);
+            g1.A = mat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.Bp), pB, v * X, v, 1, ldv, 0);
             g1.B = mat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, ldv, 0);
             g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
             g1.out = out_split(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, ldX, 1, 0, 0, (long long)v * ldX);
@@ -518,6 +535,32 @@ int p_tc(ppl_cpd* h) {
         if (e) return e;
     }
     return PPL_OK;
+}
+
+// D-bar = B_vv - 2 B_vo t1 (t1 == nullptr: D-bar = B_vv), then its operand copies
+void build_dbar(ppl_cpd* h, const double* t1) {
+    const int o = h->o, v = h->v, X = h->X, n = h->n;
+    double* Bb = h->at<double>(h->L.Bbar);
+    extract_vv(h->B, o, v, X, Bb, h->st);
+    if (t1) {
+        G64 g{};
+        g.A = h->B + (long long)o * n; g.ab = (long long)n * n; g.am = ix1(n); g.ak = ix1(1);   // B[Q][o+b][k]
+        g.B = t1; g.bn = ix1(1); g.bk = ix1(v);                                            // t1[k][d]
+        g.C = Bb; g.cb = (long long)v * v; g.cm = ix1(v); g.cn = ix1(1);
+        g.M = v; g.N = v; g.K = o; g.batch = X; g.ksplit = 1; g.alpha = -2.0; g.beta = 1.0;
+        gemm64(g, h->st);
+    }
+    if (!h->tc()) return;
+    const int prec = h->opts.precision;
+    const long long ldv = h->L.ldv, pB = (long long)X * v * ldv;
+    SplitSrc s{};
+    s.src = Bb;
+    s.rmap = ix2(v, (long long)v * v, 1); s.cmap = ix1(v);                      // rows (Q,d), K = b
+    split_to_operand(prec, s, X * v, v, 1, opb(h, h->L.BbN), pB, ldv, 0, h->st);
+    s.rmap = ix2(X, v, (long long)v * v); s.cmap = ix1(1);                      // rows (b,Q), K = d
+    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbP), pB, ldv, 0, h->st);
+    s.rmap = ix2(X, 1, (long long)v * v); s.cmap = ix1(v);                      // rows (d,Q), K = b
+    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbT), pB, ldv, 0, h->st);
 }
 
 // operand copies of tau and B (once per tau / B)
@@ -778,6 +821,7 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
         cudaMemcpyAsync(h->scal() + SC_NORM2_PREV, h->scal() + SC_TERMS + 1, sizeof(double),
                         cudaMemcpyDeviceToDevice, h->st);
         e = prepare_operands(h, false);
+        if (!e && h->dressed()) build_dbar(h, nullptr);
     }
     if (!e) e = check_cuda(h, "init");
     if (!e) e = leave(h);
@@ -935,7 +979,11 @@ int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_ou
         // G_a[c][b*v+d] = sum_Q B[Q][o+a][o+c] B[Q][o+b][o+d]
         G64 q{};
         q.A = h->B + (long long)(o + a0) * n + o; q.ab = n; q.am = ix1(1); q.ak = ix1((long long)n * n);
-        q.B = h->B + (long long)o * n + o; q.bb = 0; q.bn = ix2(v, n, 1); q.bk = ix1((long long)n * n);
+        if (h->dressed()) {
+            q.B = h->at<double>(h->L.Bbar); q.bb = 0; q.bn = ix1(1); q.bk = ix1((long long)v * v);
+        } else {
+            q.B = h->B + (long long)o * n + o; q.bb = 0; q.bn = ix2(v, n, 1); q.bk = ix1((long long)n * n);
+        }
         q.C = Gb; q.cb = v3; q.cm = ix1((long long)v * v); q.cn = ix1(1);
         q.M = v; q.N = v * v; q.K = X; q.batch = nb; q.ksplit = 1; q.alpha = 1.0;
         gemm64(q, h->st);
@@ -982,6 +1030,21 @@ int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise) {
     }
     if (symmetrise) symmetrise_pairs(R_out, v, o, h->st);
     e = check_cuda(h, "reconstruct");
+    if (!e) e = sync_and_check(h);
+    leave(h);
+    return e;
+}
+
+int ppl_cpd_set_t1(ppl_cpd* h, const double* t1) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (!h->dressed()) return fail(h, PPL_EINVAL, "the handle was created without opts.dressed");
+    h->have_normR2 = false;
+    h->normR2 = 0.0;
+    int e = enter(h);
+    if (e) return e;
+    cudaMemsetAsync(h->scal() + SC_NORMR2, 0, sizeof(double), h->st);
+    build_dbar(h, t1);
+    e = check_cuda(h, "set_t1");
     if (!e) e = sync_and_check(h);
     leave(h);
     return e;

@@ -310,6 +310,17 @@ __global__ void k_symmetrise(double* X, int v, int o) {
     }
 }
 
+__global__ void k_extract_vv(const double* B, int o, int v, int X, double* out) {
+    const int n = o + v;
+    const long long total = (long long)X * v * v;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(e % v), b = (int)((e / v) % v);
+        const long long Q = e / ((long long)v * v);
+        out[e] = B[Q * n * n + (long long)(o + b) * n + o + d];
+    }
+}
+
 __global__ void k_fill(double* p, size_t n, double val) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         p[e] = val;
@@ -398,6 +409,10 @@ void kr_pair(const double* U1, const double* U2, const double* lam, int d1, int 
 
 void symmetrise_pairs(double* X, int v, int o, cudaStream_t s) {
     k_symmetrise<<<grid_for((long long)v * v * o * o, 256), 256, 0, s>>>(X, v, o);
+}
+
+void extract_vv(const double* B, int o, int v, int X, double* out, cudaStream_t s) {
+    k_extract_vv<<<grid_for((long long)X * v * v, 256), 256, 0, s>>>(B, o, v, X, out);
 }
 
 void fill_f64(double* p, size_t n, double val, cudaStream_t s) {

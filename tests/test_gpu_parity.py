@@ -265,3 +265,31 @@ def test_autotune_picks_a_chunk_and_keeps_results():
         assert _rel(fa[k], fb[k]) < 1e-4
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_dressed_mttkrp_sweeps_and_exact(prec):
+    inp = inputs.make_inputs(4, 21, 30, 40, seed=41)
+    Bbar = orc.dress(inp.B, inp.t1, inp.o)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec, dressed=True)
+    cp.set_t1(_dev(inp.t1))
+    for m in orc.MODES:
+        assert _rel(cp.mttkrp(m).cpu().numpy(), orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m, Bbar)) < TOL_MTTKRP[prec]
+    n2, E, Rt = cp.exact_contract(want_R=True)
+    R_ref = orc.ppl_tensor(inp.Bvv, inp.tau, Bbar)
+    assert _rel(Rt.cpu().numpy(), R_ref) < 1e-13
+    assert abs(E - orc.energy_of_tensor(R_ref, inp.B, inp.o)) < 1e-12 * abs(E)
+    U_ref, lam_ref, hist = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 3, n2, Bbar=Bbar)
+    fits = cp.sweep(3)
+    if prec == "fp64":
+        f = {k: t.cpu().numpy() for k, t in cp.factors().items()}
+        for m in orc.MODES:
+            assert _rel(f[m], U_ref[m]) < 1e-8
+    assert abs(fits[-1] - hist[-1]["fit"]) < (1e-9 if prec == "fp64" else 1e-4)
+    cp.set_t1(None)                       # undressed again: back to the symmetric tensor
+    assert _rel(cp.mttkrp("a").cpu().numpy(), orc.mttkrp(inp.Bvv, inp.tau, cp_factors(cp), "a")) < TOL_MTTKRP[prec]
+    cp.close()
+
+
+def cp_factors(cp):
+    return {k: t.cpu().numpy() for k, t in cp.factors().items()}
