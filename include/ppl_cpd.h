@@ -132,6 +132,14 @@ int ppl_cpd_energy(ppl_cpd* h, double* E_cp);
  * ||R||^2 in the handle for ppl_cpd_fit.  Cost 2 X v^4 + 2 o^2 v^4 flops, FP64. */
 int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_out);
 
+/* The same exact contraction on the tensor cores, in the handle's precision
+ * (BF16X3 or TF32; EINVAL for FP64 handles): per a, G_a[b][(c,d)] =
+ * sum_Q B[Q,a,c] D-bar[Q,b,d] and R[a] = G_a tau^T with FP32 accumulation,
+ * split-K sums and the ||R||^2 / energy reductions in FP64.  Relative error of
+ * the order of the precision's unit roundoff (1e-5 for BF16X3); use
+ * ppl_exact_contract where FP64 accuracy matters and the size allows it. */
+int ppl_exact_contract_mixed(ppl_cpd* h, double* normR2, double* E_exact, double* R_out);
+
 /* The CP model in canonical form, R~[a,b,i,j] = sum_r lam_r Ua[a,r] Ub[b,r] Ui[i,r] Uj[j,r],
  * written to R_out [v][v][o][o] (FP64, device); with symmetrise != 0 it is
  * replaced by 0.5 (R~[a,b,i,j] + R~[b,a,j,i]), the post-reconstruction

@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_cpd_set_guess_policy.argtypes = [H, c_int]
     L.ppl_cpd_reconstruct.argtypes = [H, c_void_p, c_int]
     L.ppl_cpd_set_t1.argtypes = [H, c_void_p]
+    L.ppl_exact_contract_mixed.argtypes = [H, POINTER(c_double), POINTER(c_double), c_void_p]
     L.ppl_cpd_autotune.argtypes = [H, POINTER(c_int)]
     L.ppl_cpd_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int, c_void_p]
     L.ppl_cpd_batch_sweep.argtypes = [c_void_p, c_int, POINTER(c_double)]
@@ -90,7 +91,7 @@ def lib() -> ctypes.CDLL:
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
                  "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct", "ppl_cpd_autotune",
-                 "ppl_cpd_set_t1",
+                 "ppl_cpd_set_t1", "ppl_exact_contract_mixed",
                  "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy", "ppl_cpd_batch_kernels",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm"):
         getattr(L, name).restype = c_int
@@ -161,6 +162,12 @@ def ppl_cpd_energy(h) -> float:
 def ppl_exact_contract(h, R_ptr=None):
     n2, E = c_double(), c_double()
     _check(lib().ppl_exact_contract(h, ctypes.byref(n2), ctypes.byref(E), R_ptr), h)
+    return n2.value, E.value
+
+
+def ppl_exact_contract_mixed(h, R_ptr=None):
+    n2, E = c_double(), c_double()
+    _check(lib().ppl_exact_contract_mixed(h, ctypes.byref(n2), ctypes.byref(E), R_ptr), h)
     return n2.value, E.value
 
 
@@ -346,11 +353,13 @@ class CpAls:
     def energy(self) -> float:
         return ppl_cpd_energy(self.h)
 
-    def exact_contract(self, want_R: bool = False):
+    def exact_contract(self, want_R: bool = False, mixed: bool = False):
+        """||R||^2, E_exact (and R): FP64, or with mixed=True on the tensor cores."""
         Rt = None
         if want_R:
             Rt = self.torch.empty((self.v, self.v, self.o, self.o), dtype=self.torch.float64, device=self.B.device)
-        n2, E = ppl_exact_contract(self.h, Rt.data_ptr() if Rt is not None else None)
+        fn = ppl_exact_contract_mixed if mixed else ppl_exact_contract
+        n2, E = fn(self.h, Rt.data_ptr() if Rt is not None else None)
         return n2, E, Rt
 
     def set_t1(self, t1):

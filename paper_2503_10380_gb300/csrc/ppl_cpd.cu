@@ -34,6 +34,7 @@ struct Layout {
     size_t T64, W64, Y64, S64;                       // FP64 form
     size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Bbar, BbN, BbP, BbT;   // t1-dressed D-bar: FP64 [X][v][v] and its operand layouts
+    size_t Bq, BbQ, Gop;          // tensor-core exact contraction: B and D-bar as [(p,q)][Q], G_a
     size_t Za, Zb, gov, Gblk, Rblk;
     size_t ring, cache, guess0;   // 6 iterates, the Near-Optimal cache, the initial guess
     size_t recon;                 // Khatri-Rao chunks for the reconstruction
@@ -115,6 +116,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
     L.PART = none;
     L.Bbar = L.BbN = L.BbP = L.BbT = none;
+    L.Bq = L.BbQ = L.Gop = none;
     if (op.dressed) L.Bbar = take((size_t)X * v * v * d);
     if (!tc) {
         L.T64 = take((size_t)R * v * v * d);
@@ -137,7 +139,14 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.WTa = take((size_t)rc * v * L.ldX * e);
         L.WTb = take((size_t)rc * v * L.ldX * e);
         L.S = take((size_t)rc * L.ldvv * e);
-        L.PART = take((size_t)KSMAX * (size_t)(v > o * o ? v : o * o) * rc * sizeof(float));
+        {
+            const size_t chain_part = (size_t)KSMAX * (size_t)(v > o * o ? v : o * o) * rc;
+            const size_t exact_part = (size_t)KSMAX * (size_t)v * o * o;
+            L.PART = take((chain_part > exact_part ? chain_part : exact_part) * sizeof(float));
+        }
+        L.Bq = take((size_t)v * v * L.ldX * e);
+        L.Gop = take((size_t)v * L.ldvv * e);
+        if (op.dressed) L.BbQ = take((size_t)v * v * L.ldX * e);
         if (op.dressed) {
             L.BbN = take((size_t)X * v * L.ldv * e);
             L.BbP = take((size_t)v * X * L.ldv * e);
@@ -561,6 +570,8 @@ void build_dbar(ppl_cpd* h, const double* t1) {
     split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbP), pB, ldv, 0, h->st);
     s.rmap = ix2(X, 1, (long long)v * v); s.cmap = ix1(v);                      // rows (d,Q), K = b
     split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbT), pB, ldv, 0, h->st);
+    s.rmap = ix1(1); s.cmap = ix1((long long)v * v);                             // rows (b,d), K = Q
+    split_to_operand(prec, s, v * v, X, 1, opb(h, h->L.BbQ), (long long)v * v * h->L.ldX, h->L.ldX, 0, h->st);
 }
 
 // operand copies of tau and B (once per tau / B)
@@ -579,6 +590,9 @@ int prepare_operands(ppl_cpd* h, bool tau_only) {
     split_to_operand(prec, s, X * v, v, 1, opb(h, h->L.Bn), pB, ldv, 0, h->st);
     s.rmap = ix2(X, n, (long long)n * n);
     split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.Bp), pB, ldv, 0, h->st);
+    // B as [(p,q)][Q] for the tensor-core exact contraction
+    s.rmap = ix2(v, n, 1); s.cmap = ix1((long long)n * n);
+    split_to_operand(prec, s, v * v, X, 1, opb(h, h->L.Bq), (long long)v * v * h->L.ldX, h->L.ldX, 0, h->st);
     // scratch whose padding must read as zero
     zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * ldv * 4, h->st);
     zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * ldvv * 4, h->st);
@@ -1033,6 +1047,55 @@ int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise) {
     if (!e) e = sync_and_check(h);
     leave(h);
     return e;
+}
+
+int ppl_exact_contract_mixed(ppl_cpd* h, double* normR2, double* E_exact, double* R_out) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    if (!h->tc()) return fail(h, PPL_EINVAL, "ppl_exact_contract_mixed needs a BF16X3 or TF32 handle");
+    const int o = h->o, v = h->v, X = h->X, n = h->n;
+    const long long ldX = h->L.ldX, ldvv = h->L.ldvv, vo2 = (long long)v * o * o;
+    int e = enter(h);
+    if (e) return e;
+    double* gov = h->at<double>(h->L.gov);
+    double* acc = h->scal() + SC_EXACT;
+    cudaMemsetAsync(acc, 0, 2 * sizeof(double), h->st);
+    G64 g{};
+    g.A = h->B + o; g.am = ix2(v, n, 1); g.ak = ix1((long long)n * n);
+    g.B = h->B + o; g.bn = ix2(v, n, 1); g.bk = ix1((long long)n * n);
+    g.C = gov; g.cm = ix1((long long)o * v); g.cn = ix1(1);
+    g.M = o * v; g.N = o * v; g.K = X; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
+    gemm64(g, h->st);
+    const long long pQ = (long long)v * v * ldX, pG = (long long)v * ldvv;
+    for (int a = 0; a < v && !e; ++a) {
+        // G_a[b][c*v + d] = sum_Q D-bar[Q][b][d] B[Q][a][c]
+        TcGemm g1{};
+        g1.A = mat(opb(h, h->dressed() ? h->L.BbQ : h->L.Bq), pQ, v * v, X, 1, ldX, 0);
+        g1.B = mat(opb(h, h->L.Bq), pQ, v, X, v, ldX, (long long)v * ldX);
+        g1.b_b0 = a;
+        g1.M = v * v; g1.N = v; g1.K = X; g1.batch = 1; g1.ksplit = 1;
+        g1.out = out_split(opb(h, h->L.Gop), pG, 0, v, ldvv, 1, 0, 0, v);
+        e = run_tc(h, g1, "exact G");
+        if (e) break;
+        // R[a][b][ij] = sum_{cd} G_a[b][cd] tau[ij][cd], split-K summed in FP64
+        double* Rdst = R_out ? R_out + (long long)a * vo2 : h->at<double>(h->L.Rblk);
+        TcGemm g2{};
+        g2.A = mat(opb(h, h->L.Gop), pG, v, v * v, 1, ldvv, 0);
+        g2.B = mat(opb(h, h->L.tauN), (long long)o * o * ldvv, o * o, v * v, 1, ldvv, 0);
+        g2.M = v; g2.N = o * o; g2.K = v * v; g2.batch = 1;
+        e = run_tc_partial(h, g2, Rdst, (long long)o * o, "exact R");
+        if (e) break;
+        exact_reduce(Rdst, a, 1, v, o, gov, h->at<double>(h->L.partial), acc, h->st);
+    }
+    if (!e) e = check_cuda(h, "exact_contract_mixed");
+    if (!e) e = sync_and_check(h);
+    double res[2] = {0, 0};
+    if (!e) cudaMemcpy(res, acc, sizeof res, cudaMemcpyDeviceToHost);
+    leave(h);
+    if (e) return e;
+    if (normR2) *normR2 = res[0];
+    if (E_exact) *E_exact = res[1];
+    if (res[0] > 0.0) return ppl_cpd_set_normR2(h, res[0]);
+    return PPL_OK;
 }
 
 int ppl_cpd_set_t1(ppl_cpd* h, const double* t1) {

@@ -293,3 +293,20 @@ def test_dressed_mttkrp_sweeps_and_exact(prec):
 
 def cp_factors(cp):
     return {k: t.cpu().numpy() for k, t in cp.factors().items()}
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("tf32", 4e-3)])
+@pytest.mark.parametrize("dressed", [False, True])
+def test_exact_contraction_on_tensor_cores(prec, tol, dressed):
+    inp = inputs.make_inputs(5, 26, 70, 30, seed=44)
+    Bbar = orc.dress(inp.B, inp.t1, inp.o) if dressed else None
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec, dressed=dressed)
+    if dressed:
+        cp.set_t1(_dev(inp.t1))
+    n2, E, Rt = cp.exact_contract(want_R=True, mixed=True)
+    R_ref = orc.ppl_tensor(inp.Bvv, inp.tau, Bbar)
+    assert _rel(Rt.cpu().numpy(), R_ref) < tol
+    assert abs(n2 - float(np.sum(R_ref ** 2))) < 2 * tol * n2
+    E_ref = orc.energy_of_tensor(R_ref, inp.B, inp.o)
+    assert abs(E - E_ref) < 2 * tol * abs(E_ref)
+    cp.close()
