@@ -478,6 +478,200 @@ def run_batch(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+PREC_CFG, PREC_SWEEPS = (40, 400, 1200, 1600), 20
+SEQ_CFG, SEQ_STEPS, SEQ_MAX_SWEEPS, SEQ_EPS = (60, 600, 1800, 2400), 15, 50, 1e-6
+
+
+def _factors_host(cp):
+    return {k: t.cpu().numpy().copy() for k, t in cp.factors().items()}
+
+
+def _timed_sweeps(cp, n, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cp.sweep(n, want_hist=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def run_precision(args, world, rank, local):
+    """o=40 v=400 X=1200 R=1600: BF16x3 and TF32 against the plain FP64 GPU form
+    from the same start after PREC_SWEEPS sweeps (energy in kcal/mol, relative
+    error of every factor), and the sweep rate of each form."""
+    import numpy as np
+    import torch
+    from paper_2503_10380_gb300 import binding, inputs
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    o, v, X, R = PREC_CFG
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=dev)
+    # ||R||^2 and E_exact from the tensor-core exact contraction (relative error ~1e-5)
+    cp = binding.CpAls(B, tau, fac, precision="bf16x3")
+    normR2, E_exact, _ = cp.exact_contract(mixed=True)
+    cp.close()
+    del cp
+    f64 = binding.CpAls(B, tau, fac, precision="fp64")
+    f64.set_normR2(normR2)
+    f64.sweep(1, want_hist=False)
+    torch.cuda.synchronize()
+    f64_ms = _timed_sweeps(f64, PREC_SWEEPS - 1, stream)
+    E64, F64, fit64 = f64.energy(), _factors_host(f64), f64.fit()
+    f64.close()
+    del f64
+    torch.cuda.empty_cache()
+    variants = {}
+    clocks = None
+    for prec in ("bf16x3", "tf32"):
+        cp = binding.CpAls(B, tau, fac, precision=prec, profile=True)
+        cp.set_normR2(normR2)
+        cp.sweep(PREC_SWEEPS, want_hist=False)
+        E, F, fit = cp.energy(), _factors_host(cp), cp.fit()
+        cp.sweep(args.warmup, want_hist=False)
+        torch.cuda.synchronize()
+        ck = ClockSampler(local) if prec == "bf16x3" else None
+        ms = _timed_sweeps(cp, args.steps, stream)
+        if ck is not None:
+            clocks = ck.stop()
+        acc = None
+        for _ in range(3):
+            cp.sweep(1, want_hist=False)
+            ph = cp.phase_ms()
+            acc = ph if acc is None else {k: acc[k] + ph[k] for k in acc}
+        mt_ms = sum(acc[k] for k in ("tau_r", "chain_a", "chain_b", "s_and_p")) / 3
+        launches = int(cp.stats()["kernels_per_sweep"])
+        cp.close()
+        del cp
+        variants[prec] = {
+            "ms_per_sweep": ms, "sweeps_per_s": 1000.0 / ms,
+            "mttkrp_tflops": alg_flops(o, v, X, R) / (mt_ms / 1000.0) / 1e12,
+            "speedup_vs_fp64_gpu": f64_ms / ms, "E_cp": E, "fit": fit,
+            "dE_kcal_per_mol": abs(E - E64) * KCAL, "dE_rel": abs(E - E64) / abs(E64),
+            "factor_rel_err": {m: float(np.linalg.norm(F[m] - F64[m]) / np.linalg.norm(F64[m])) for m in F64},
+            "kernels_per_sweep": launches,
+        }
+    ms = reduce_max(variants["bf16x3"]["ms_per_sweep"], world, dev)
+    pk, pk_kind = peaks()
+    peak = pk["bf16_tflops_sustained"] / 3.0
+    tf = variants["bf16x3"]["mttkrp_tflops"]
+    line = {
+        "metric": METRIC, "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic (seeded; shapes of the paper's molecules)",
+        "config": {"workload": f"cp-als-ppl precision study o={o} v={v} X={X} R={R}, {PREC_SWEEPS} sweeps "
+                               f"from one start in FP64, BF16x3 and TF32", "o": o, "v": v, "X": X, "R": R,
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                     "traffic": None, "kernel": "all MTTKRP contractions of one sweep (phase events)",
+                     "peak_source": f"{pk_kind}: sustained bf16 / 3"},
+        "fp64_gpu": {"ms_per_sweep": f64_ms, "E_cp": E64, "fit": fit64},
+        "variants": variants,
+        "E_exact_bf16x3": E_exact, "normR2_bf16x3": normR2,
+        "rank_error_kcal_per_mol": abs(E64 - E_exact) * KCAL,
+        "gpu_launches": variants["bf16x3"]["kernels_per_sweep"] * args.steps,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_sequence(args, world, rank, local):
+    """o=60 v=600 X=1800 R=2400: SEQ_STEPS CC-like steps tau_k = tau_{k-1} + dtau_k,
+    each a CPD warm-started from the previous factors on the device and swept
+    until |dfit| < SEQ_EPS (at most SEQ_MAX_SWEEPS sweeps); ||R_k||^2 from the
+    tensor-core exact contraction at every step."""
+    import torch
+    from paper_2503_10380_gb300 import binding, inputs
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    o, v, X, R = SEQ_CFG
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=dev)
+    rms0 = float(torch.sqrt(torch.mean(tau * tau)))
+    torch.cuda.empty_cache()
+    cp = binding.CpAls(B, tau, fac, precision=args.precision, profile=True)
+    clocks = ClockSampler(local)
+    steps, t_solve, t_exact, n_sweeps = [], 0.0, 0.0, 0
+    for k in range(SEQ_STEPS):
+        if k > 0:
+            tau += inputs.tau_increment_t(torch, rms0, tuple(tau.shape), k, seed=SEED, device=dev)
+            cp.set_tau(tau)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        normR2, E_exact, _ = cp.exact_contract(mixed=True)
+        t1 = time.perf_counter()
+        sweeps, fits, _ = cp.solve(SEQ_MAX_SWEEPS, "dfit", SEQ_EPS)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        E = cp.energy()
+        t_exact += t1 - t0
+        t_solve += t2 - t1
+        n_sweeps += sweeps
+        steps.append({"k": k, "sweeps": sweeps, "stop": "dfit" if sweeps < SEQ_MAX_SWEEPS else "max_sweeps",
+                      "fit": fits[sweeps - 1] if sweeps else None,
+                      "dfit_last": abs(fits[sweeps - 1] - fits[sweeps - 2]) if sweeps > 1 else None,
+                      "E_cp": E, "E_exact_bf16x3": E_exact, "solve_s": t2 - t1, "exact_s": t1 - t0})
+        if rank == 0:
+            print(json.dumps({"progress": steps[-1]}), file=sys.stderr, flush=True)
+    ck = clocks.stop()
+    acc = None
+    for _ in range(3):
+        cp.sweep(1, want_hist=False)
+        ph = cp.phase_ms()
+        acc = ph if acc is None else {kk: acc[kk] + ph[kk] for kk in acc}
+    phases = {kk: acc[kk] / 3 for kk in acc}
+    mt_ms = phases["tau_r"] + phases["chain_a"] + phases["chain_b"] + phases["s_and_p"]
+    ms_sweep = _timed_sweeps(cp, 3, stream)
+    launches = int(cp.stats()["kernels_per_sweep"])
+    cp.close()
+    del cp
+    torch.cuda.empty_cache()
+    f64 = binding.CpAls(B, tau, fac, precision="fp64")
+    f64.sweep(1, want_hist=False)
+    torch.cuda.synchronize()
+    f64_ms = _timed_sweeps(f64, 1, stream)
+    f64.close()
+    t_solve = reduce_max(t_solve, world, dev)
+    pk, pk_kind = peaks()
+    peak = pk["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+    tf = alg_flops(o, v, X, R) / (mt_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": world * n_sweeps / t_solve, "unit": "sweeps/s", "n_gpus": world,
+        "steps": SEQ_STEPS, "warmup": 0, "ms_per_step": 1000.0 * t_solve / n_sweeps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic (seeded; shapes of the paper's molecules)",
+        "config": {"workload": f"cp-als-ppl warm-started CC-like sequence o={o} v={v} X={X} R={R}, {SEQ_STEPS} steps, "
+                               f"|dfit| < {SEQ_EPS} or {SEQ_MAX_SWEEPS} sweeps", "o": o, "v": v, "X": X, "R": R,
+                   "l2": "inputs larger than L2 (tau 10.4 GB)"},
+        "sweeps_total": n_sweeps, "solve_s": t_solve, "exact_contract_s": t_exact,
+        "ms_per_sweep_steady": ms_sweep, "phase_ms": phases,
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                     "traffic": None, "kernel": "all MTTKRP contractions of one sweep (phase events)",
+                     "peak_source": f"{pk_kind}"},
+        "fp64_gpu": {"ms_per_sweep": f64_ms, "speedup_mixed_vs_fp64": f64_ms / ms_sweep},
+        "per_step": steps,
+        "gpu_launches": launches * n_sweeps,
+        "clocks": {kk: ck[kk] for kk in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,8 +681,10 @@ def main():
     ap.add_argument("--precision", choices=["bf16x3", "tf32"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
-                    help="single: o=20 v=200 X=600 R=800 (default); batch: 64 uneven instances")
+    ap.add_argument("--workload", choices=["single", "batch", "precision", "sequence"], default="single",
+                    help="single: o=20 v=200 X=600 R=800 (default); batch: 64 uneven instances; "
+                         "precision: o=40 v=400 X=1200 R=1600 in FP64, BF16x3 and TF32; "
+                         "sequence: o=60 v=600 X=1800 R=2400, 15 warm-started CC-like steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -502,6 +698,10 @@ def main():
             run_reference(args, world, rank)
         elif args.workload == "batch":
             run_batch(args, world, rank, local)
+        elif args.workload == "precision":
+            run_precision(args, world, rank, local)
+        elif args.workload == "sequence":
+            run_sequence(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -49,6 +49,9 @@ extern "C" {
 #define PPL_PREC_FP64   0  /* plain FP64 on the CUDA cores                                 */
 #define PPL_PREC_BF16X3 1  /* tcgen05 BF16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accum. */
 #define PPL_PREC_TF32   2  /* tcgen05 TF32 (round-to-nearest operands), FP32 accumulate    */
+#define PPL_PREC_TF32X3 3  /* tcgen05 TF32 hi/lo split (22 bits), three products, FP32
+                              accumulate restarted every acc_chunk K blocks and summed
+                              with round-to-nearest                                        */
 
 #define PPL_MODE_A 0  /* alpha, first virtual index  */
 #define PPL_MODE_B 1  /* beta, second virtual index  */
@@ -64,7 +67,11 @@ typedef struct {
     int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
     int profile;     /* 1: record CUDA events between the phases of every sweep           */
     int dressed;     /* 1: reserve room for the t1-dressed D-bar (ppl_cpd_set_t1)         */
-    int reserved[10];
+    int acc_chunk;   /* K blocks (64 bf16 / 32 tf32 columns) summed in one tensor-core
+                        accumulator before the epilogue adds it to FP32 registers with
+                        round-to-nearest; 0 = the precision's default (TF32X3: 1,
+                        otherwise no restart), -1 = never restart                       */
+    int reserved[9];
 } ppl_cpd_opts;
 
 typedef struct {
@@ -258,9 +265,10 @@ int ppl_cp_energy_static(int o, int v, int X, int R, const double* B, const doub
 
 /* Building-block check of the tensor-core contraction used by the MTTKRP:
  * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the
- * given PPL_PREC_BF16X3 or PPL_PREC_TF32 tcgen05 kernel (operands split or
- * rounded on the device, FP32 accumulate) and written to C (FP32 device,
- * [M][N]).  workspace must hold ppl_tc_gemm_workspace_size bytes. */
+ * given PPL_PREC_BF16X3, PPL_PREC_TF32 or PPL_PREC_TF32X3 tcgen05 kernel
+ * (operands split or rounded on the device, FP32 accumulate; TF32X3 restarts
+ * the accumulator every K block as a handle does by default) and written to
+ * C (FP32 device, [M][N]).  workspace must hold ppl_tc_gemm_workspace_size bytes. */
 int ppl_tc_gemm_workspace_size(int M, int N, int K, int precision, size_t* bytes);
 int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float* B, float* C,
                 void* workspace, size_t ws_bytes, void* stream);

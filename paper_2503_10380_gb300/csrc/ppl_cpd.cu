@@ -124,7 +124,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.Y64 = take((size_t)rc * X * v * d);
         L.S64 = take((size_t)rc * v * v * d);
     } else {
-        const size_t e = 4;   // bf16 hi + lo, or one fp32
+        const size_t e = op.precision == PPL_PREC_TF32X3 ? 8 : 4;   // bf16 hi + lo, fp32 hi + lo, or one fp32
         L.tauT = take((size_t)v * v * L.ldo2 * e);
         L.tauN = take((size_t)o * o * L.ldvv * e);
         L.Bn = take((size_t)X * v * L.ldv * e);
@@ -197,6 +197,14 @@ struct ppl_cpd {
     unsigned int* errflag() const { return reinterpret_cast<unsigned int*>(ws + L.flags + 8); }
     int dim(int m) const { return m < 2 ? v : o; }
     bool tc() const { return opts.precision != PPL_PREC_FP64; }
+    // bytes of one operand element over all its planes
+    size_t opbytes() const { return opts.precision == PPL_PREC_TF32X3 ? 8 : 4; }
+    // K blocks per tensor-core accumulation chunk (0: one chunk per tile)
+    int kchunk() const {
+        if (opts.acc_chunk > 0) return opts.acc_chunk;
+        if (opts.acc_chunk < 0) return 0;
+        return opts.precision == PPL_PREC_TF32X3 ? 1 : 0;
+    }
     bool dressed() const { return opts.dressed != 0; }
 };
 
@@ -271,6 +279,7 @@ int bn_for(int N) {
 
 int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
     g.prec = h->opts.precision;
+    g.kchunk = h->kchunk();
     if (g.bn == 0) g.bn = bn_for(g.N);
     const int r = tc_gemm(g, h->errflag(), h->st);
     if (r != 0)
@@ -594,11 +603,11 @@ int prepare_operands(ppl_cpd* h, bool tau_only) {
     s.rmap = ix2(v, n, 1); s.cmap = ix1((long long)n * n);
     split_to_operand(prec, s, v * v, X, 1, opb(h, h->L.Bq), (long long)v * v * h->L.ldX, h->L.ldX, 0, h->st);
     // scratch whose padding must read as zero
-    zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * ldv * 4, h->st);
-    zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * ldvv * 4, h->st);
-    zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * ldv * 4, h->st);
-    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * h->L.ldX * 4, h->st);
-    zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * h->L.ldX * 4, h->st);
+    zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * ldv * h->opbytes(), h->st);
+    zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * ldvv * h->opbytes(), h->st);
+    zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * ldv * h->opbytes(), h->st);
+    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * h->L.ldX * h->opbytes(), h->st);
+    zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * h->L.ldX * h->opbytes(), h->st);
     return PPL_OK;
 }
 
@@ -762,7 +771,7 @@ int ppl_cpd_workspace_size(int o, int v, int X, int R, const ppl_cpd_opts* opts,
     ppl_cpd_default_opts(&op);
     if (opts) op = *opts;
     if (!bytes) return fail(nullptr, PPL_EINVAL, "bytes is NULL");
-    if (op.precision < 0 || op.precision > 2) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
+    if (op.precision < 0 || op.precision > 3) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
     Layout L;
     if (!plan(o, v, X, R, op, L)) return fail(nullptr, PPL_EINVAL, "sizes out of range (o=%d v=%d X=%d R=%d)", o, v, X, R);
     *bytes = L.total;
@@ -776,7 +785,7 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     ppl_cpd_opts op;
     ppl_cpd_default_opts(&op);
     if (opts) op = *opts;
-    if (op.precision < 0 || op.precision > 2) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
+    if (op.precision < 0 || op.precision > 3) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
     if (!B || !tau || !factors || !workspace) return fail(nullptr, PPL_EINVAL, "NULL device pointer");
     if (((uintptr_t)workspace) % 256) return fail(nullptr, PPL_EINVAL, "workspace not 256-byte aligned");
     Layout L;
@@ -1051,7 +1060,7 @@ int ppl_cpd_reconstruct(ppl_cpd* h, double* R_out, int symmetrise) {
 
 int ppl_exact_contract_mixed(ppl_cpd* h, double* normR2, double* E_exact, double* R_out) {
     if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
-    if (!h->tc()) return fail(h, PPL_EINVAL, "ppl_exact_contract_mixed needs a BF16X3 or TF32 handle");
+    if (!h->tc()) return fail(h, PPL_EINVAL, "ppl_exact_contract_mixed needs a tensor-core (BF16X3, TF32 or TF32X3) handle");
     const int o = h->o, v = h->v, X = h->X, n = h->n;
     const long long ldX = h->L.ldX, ldvv = h->L.ldvv, vo2 = (long long)v * o * o;
     int e = enter(h);
@@ -1460,10 +1469,12 @@ int ppl_cpd_phase_ms(ppl_cpd* h, double* ms) {
 }
 
 int ppl_tc_gemm_workspace_size(int M, int N, int K, int precision, size_t* bytes) {
-    if (!bytes || M < 1 || N < 1 || K < 1 || (precision != PPL_PREC_BF16X3 && precision != PPL_PREC_TF32))
+    if (!bytes || M < 1 || N < 1 || K < 1 ||
+        (precision != PPL_PREC_BF16X3 && precision != PPL_PREC_TF32 && precision != PPL_PREC_TF32X3))
         return fail(nullptr, PPL_EINVAL, "bad arguments");
     const long long ld = rup(K, 8);
-    *bytes = (size_t)rup((long long)M * ld * 4, 256) + (size_t)rup((long long)N * ld * 4, 256) + 256;
+    const long long eb = precision == PPL_PREC_TF32X3 ? 8 : 4;
+    *bytes = (size_t)rup((long long)M * ld * eb, 256) + (size_t)rup((long long)N * ld * eb, 256) + 256;
     return PPL_OK;
 }
 
@@ -1478,10 +1489,11 @@ int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float*
     if (tc_init_driver() != 0) return fail(nullptr, PPL_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cudaStream_t s = (cudaStream_t)stream;
     const long long ld = rup(K, 8);
+    const long long eb = precision == PPL_PREC_TF32X3 ? 8 : 4;
     char* w = (char*)workspace;
     void* Aop = w;
-    void* Bop = w + rup((long long)M * ld * 4, 256);
-    unsigned int* flag = (unsigned int*)(w + rup((long long)M * ld * 4, 256) + rup((long long)N * ld * 4, 256));
+    void* Bop = w + rup((long long)M * ld * eb, 256);
+    unsigned int* flag = (unsigned int*)(w + rup((long long)M * ld * eb, 256) + rup((long long)N * ld * eb, 256));
     cudaMemsetAsync(flag, 0, sizeof(unsigned int), s);
     SplitSrc sa{};
     sa.src32 = A; sa.rmap = ix1(K); sa.cmap = ix1(1);
@@ -1494,6 +1506,7 @@ int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float*
     g.A = mat(Aop, (long long)M * ld, M, K, 1, ld, 0);
     g.B = mat(Bop, (long long)N * ld, N, K, 1, ld, 0);
     g.M = M; g.N = N; g.K = K; g.batch = 1; g.ksplit = 1;
+    g.kchunk = precision == PPL_PREC_TF32X3 ? 1 : 0;
     g.out = TcOut{};
     g.out.kind = EPI_F32; g.out.out = C; g.out.sm_lo = N; g.out.sn_lo = 1; g.out.alpha = 1.0f;
     g.bn = bn_for(N);

@@ -71,8 +71,9 @@ void extract_vv(const double* B, int o, int v, int X, double* out, cudaStream_t 
 
 // ---- tensor-core path (ppl_tc.cu) ------------------------------------------
 // Operands of the tcgen05 GEMM are K-major: rows of K contiguous elements.
-// BF16X3 keeps two planes (hi, lo) of bf16; TF32 keeps one plane of fp32
-// (already rounded to tf32).  A "plane" below is the hi plane; lo = hi + plane_elems.
+// BF16X3 keeps two planes (hi, lo) of bf16, TF32X3 two planes of fp32 holding
+// tf32 values, TF32 one plane of fp32 (already rounded to tf32).  A "plane"
+// below is the hi plane; lo = hi + plane_elems.
 struct TcMat {
     void* ptr;              // hi plane (bf16) or fp32 plane
     long long plane_elems;  // distance to the lo plane in elements (BF16X3)
@@ -101,6 +102,7 @@ struct TcGemm {
     int a_bstep, b_bstep;
     int ksplit;             // split-K factor (atomic epilogues only)
     int bn;                 // N tile (multiple of 16, <= 256); 0 = automatic
+    int kchunk;             // > 0: restart the accumulator every kchunk K blocks, sum chunks in registers
     TcOut out;
 };
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);

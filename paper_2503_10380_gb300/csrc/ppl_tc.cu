@@ -8,7 +8,15 @@
 //           hi*hi + hi*lo + lo*hi (three MMAs into one accumulator), after
 //           Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial
 //           intelligence datatype for higher-precision computations" (2019);
-//   TF32:   operands rounded to tf32 (round to nearest) when written, one MMA.
+//           within each K block the cross products are issued before hi*hi;
+//   TF32:   operands rounded to tf32 (round to nearest) when written, one MMA;
+//   TF32X3: x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (22 significant
+//           bits, the FP32 exponent range), three kind::tf32 MMAs as above.
+// The FP32 accumulator of tcgen05.mma rounds toward zero at every MMA, so a
+// long sum drifts toward zero by about half an ulp per instruction.  With a
+// positive kchunk the mainloop restarts the accumulator every kchunk K blocks
+// (ping-ponging the two TMEM buffers) and the epilogue warps add the chunks in
+// FP32 registers with round-to-nearest, which removes that bias.
 // Persistent: one CTA per SM walks the 128 x bn output tiles.  Lane 0 of warp
 // 0 issues TMA into a ring of shared-memory stages, lane 0 of warp 1 issues the
 // MMAs into one of two TMEM accumulators, and warps 2..9 drain the other
@@ -46,7 +54,16 @@ struct KParams {
     long long plane, sb, sk, sm_hi, sm_lo, sn_hi, sn_lo;
     int mdiv, ndiv;
     float alpha;
+    int kchunk;             // K blocks per accumulation chunk (drained kernels)
     unsigned int* err;
+};
+
+// operand traits of the precisions
+template <int PREC> struct Prec {
+    static constexpr int PLANES = (PREC == PPL_PREC_BF16X3 || PREC == PPL_PREC_TF32X3) ? 2 : 1;
+    static constexpr bool HALF = (PREC == PPL_PREC_BF16X3);   // 2-byte elements
+    static constexpr int KE = HALF ? 64 : 32;                  // elements per 128-byte row
+    static constexpr int KSTEP = HALF ? 16 : 8;                // K per MMA instruction
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -112,7 +129,7 @@ __device__ __forceinline__ unsigned long long make_desc(uint32_t saddr) {
 template <int PREC>
 __device__ __forceinline__ void mma(uint32_t tmem, unsigned long long ad, unsigned long long bd, uint32_t idesc,
                                     uint32_t acc) {
-    if constexpr (PREC == PPL_PREC_BF16X3) {
+    if constexpr (Prec<PREC>::HALF) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -152,14 +169,59 @@ __device__ __forceinline__ float round_tf32(float x) {
     return __uint_as_float(y);
 }
 
+// the epilogue's store of 32 consecutive columns of one row
 template <int PREC>
+__device__ __forceinline__ void emit32(const KParams& p, long long idx, long long sn, int nvalid, const float (&x)[32]) {
+    if (p.kind == EPI_SPLIT) {
+        if constexpr (PREC == PPL_PREC_BF16X3) {
+            __nv_bfloat16* o = (__nv_bfloat16*)p.out + idx;
+            __nv_bfloat16* ol = o + p.plane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nvalid) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+                    o[j * sn] = hi;
+                    ol[j * sn] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+                }
+            }
+        } else if constexpr (PREC == PPL_PREC_TF32X3) {
+            float* o = (float*)p.out + idx;
+            float* ol = o + p.plane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nvalid) {
+                    const float hi = round_tf32(x[j]);
+                    o[j * sn] = hi;
+                    ol[j * sn] = round_tf32(x[j] - hi);
+                }
+            }
+        } else {
+            float* o = (float*)p.out + idx;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nvalid) o[j * sn] = round_tf32(x[j]);
+        }
+    } else if (p.kind == EPI_F32) {
+        float* o = (float*)p.out + idx;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nvalid) o[j * sn] = x[j];
+    } else {
+        double* o = (double*)p.out + idx;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nvalid) atomicAdd(o + j * sn, (double)x[j]);
+    }
+}
+
+template <int PREC, bool DRAIN>
 __global__ void __launch_bounds__(320, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
-    constexpr bool SPLIT = (PREC == PPL_PREC_BF16X3);
-    constexpr int KE = SPLIT ? 64 : 32;       // elements per 128-byte row
-    constexpr int KSTEP = SPLIT ? 16 : 8;     // K per MMA instruction
-    constexpr int ASTEP_BYTES = KSTEP * (SPLIT ? 2 : 4);   // 32 bytes
+    constexpr bool SPLIT = (Prec<PREC>::PLANES == 2);
+    constexpr int KE = Prec<PREC>::KE;
+    constexpr int KSTEP = Prec<PREC>::KSTEP;
+    constexpr int ASTEP_BYTES = 32;           // one MMA's K slice of a 128-byte row
 
     constexpr int NEPI = 8;                   // epilogue warps: two per TMEM lane quarter
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -255,53 +317,67 @@ __global__ void __launch_bounds__(320, 1)
         if (lane == 0) {
             // MMA issuer
             uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
-            idesc |= SPLIT ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
-            int it = 0, li = 0;
-            for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
+            idesc |= Prec<PREC>::HALF ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+            int it = 0, li = 0;   // li counts accumulation chunks (one per tile unless DRAIN)
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok && !*vfail; t += gridDim.x) {
                 const int z = t / tiles_mn;
                 const int ks = z % p.ksplit;
                 const int kb0 = ks * p.per_split;
                 const int nk = min(p.per_split, p.nkb_total - kb0);
-                const int buf = li & 1;
-                if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
-                    atomicOr(p.err, 8u);
-                    *vfail = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + (uint32_t)buf * acc_cols;
-                bool ok = true;
-                for (int kbi = 0; kbi < nk; ++kbi, ++it) {
-                    const int s = it % S;
-                    if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
-                        atomicOr(p.err, 2u);
+                const int kch = DRAIN ? p.kchunk : nk;
+                for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
+                    const int kc1 = min(nk, kc0 + kch);
+                    const int buf = li & 1;
+                    if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
+                        atomicOr(p.err, 8u);
                         *vfail = 1;
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = base + stage_bytes * s;
-                    const uint32_t sah = sa, sal = sa + a_bytes;
-                    const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
-                    const int kc = (kb0 + kbi) * KE;
-                    int ksteps = KE / KSTEP;
-                    if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
-                    const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
-                    const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                        mma<PREC>(d, dah + off, dbh + off, idesc, (kbi > 0 || kk > 0) ? 1u : 0u);
-                        if constexpr (SPLIT) {
-                            mma<PREC>(d, dah + off, dbl + off, idesc, 1u);
-                            mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                    const uint32_t d = tmem + (uint32_t)buf * acc_cols;
+                    for (int kbi = kc0; kbi < kc1; ++kbi, ++it) {
+                        const int s = it % S;
+                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
+                            atomicOr(p.err, 2u);
+                            *vfail = 1;
+                            ok = false;
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = base + stage_bytes * s;
+                        const uint32_t sah = sa, sal = sa + a_bytes;
+                        const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+                        const int kc = (kb0 + kbi) * KE;
+                        int ksteps = KE / KSTEP;
+                        if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+                        const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+                        const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+                        if constexpr (SPLIT) {
+                            // the small cross products first, while the accumulator is small,
+                            // then hi*hi: fewer round-toward-zero additions at full magnitude
+                            for (int kk = 0; kk < ksteps; ++kk) {
+                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                mma<PREC>(d, dah + off, dbl + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
+                                mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                            }
+                            for (int kk = 0; kk < ksteps; ++kk) {
+                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                            }
+                        } else {
+                            for (int kk = 0; kk < ksteps; ++kk) {
+                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                mma<PREC>(d, dah + off, dbh + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
+                            }
+                        }
+                        mma_commit(empty0 + 8u * s);
+                        s_consumed = it + 1;
                     }
-                    mma_commit(empty0 + 8u * s);
-                    s_consumed = it + 1;
+                    if (!ok) break;
+                    mma_commit(tfull0 + 8u * buf);
                 }
-                if (!ok) break;
-                mma_commit(tfull0 + 8u * buf);
-                ++li;
             }
             mma_commit(drain_bar);   // completes once every MMA issued here has finished
         }
@@ -310,67 +386,68 @@ __global__ void __launch_bounds__(320, 1)
         // other 32-column chunk of the accumulator
         const int q = warp & 3, half = (warp - 2) >> 2;
         int li = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        float racc[DRAIN ? 4 : 1][32];   // running sums of the chunks (DRAIN only)
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const int z = t / tiles_mn, rem = t % tiles_mn;
             const int m0 = (rem % ntm) * TM, n0 = (rem / ntm) * p.bn;
             const int bz = z / p.ksplit, ks = z % p.ksplit;
-            const int buf = li & 1;
-            if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
-                if (lane == 0) atomicOr(p.err, 4u);
-                *vfail = 1;
-                break;
-            }
-            if (*vfail) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int nk = min(p.per_split, p.nkb_total - ks * p.per_split);
+            const int nch = DRAIN ? (nk + p.kchunk - 1) / p.kchunk : 1;
             const int m = m0 + q * 32 + lane;
             const bool mrow = (m < p.M);
             long long mo = 0;
             if (mrow)
                 mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(m / p.mdiv) * p.sm_hi +
                      (long long)(m % p.mdiv) * p.sm_lo;
-            const uint32_t tb = tmem + (uint32_t)buf * acc_cols + ((uint32_t)(q * 32) << 16);
             const long long sn = p.sn_lo;
-            for (int c0 = half * 32; c0 < p.bn; c0 += 64) {
-                uint32_t v[32];
-                tmem_ld32(tb + (uint32_t)c0, v);
-                const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));   // this tile's columns only
-                if (!mrow || nvalid <= 0) continue;
-                long long idx = mo + (long long)(n0 + c0) * sn;
-                if (p.kind == EPI_SPLIT) {
-                    if constexpr (SPLIT) {
-                        __nv_bfloat16* o = (__nv_bfloat16*)p.out + idx;
-                        __nv_bfloat16* ol = o + p.plane;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if (j < nvalid) {
-                                const float x = __uint_as_float(v[j]);
-                                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                                o[j * sn] = hi;
-                                ol[j * sn] = __float2bfloat16_rn(x - __bfloat162float(hi));
-                            }
-                        }
-                    } else {
-                        float* o = (float*)p.out + idx;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < nvalid) o[j * sn] = round_tf32(__uint_as_float(v[j]));
-                    }
-                } else if (p.kind == EPI_F32) {
-                    float* o = (float*)p.out + idx;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j < nvalid) o[j * sn] = __uint_as_float(v[j]);
-                } else {
-                    double* o = (double*)p.out + idx;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j < nvalid) atomicAdd(o + j * sn, (double)__uint_as_float(v[j]));
+            for (int c = 0; c < nch; ++c, ++li) {
+                const int buf = li & 1;
+                if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
+                    if (lane == 0) atomicOr(p.err, 4u);
+                    *vfail = 1;
+                    ok = false;
+                    break;
                 }
+                if (*vfail) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tb = tmem + (uint32_t)buf * acc_cols + ((uint32_t)(q * 32) << 16);
+                const bool last = (c == nch - 1);
+                if constexpr (DRAIN) {
+#pragma unroll
+                    for (int sl = 0; sl < 4; ++sl) {
+                        const int c0 = half * 32 + sl * 64;
+                        if (c0 < p.bn) {
+                            uint32_t v[32];
+                            tmem_ld32(tb + (uint32_t)c0, v);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                racc[sl][j] = (c == 0 ? 0.0f : racc[sl][j]) + __uint_as_float(v[j]);
+                            const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
+                            if (last && mrow && nvalid > 0)
+                                emit32<PREC>(p, mo + (long long)(n0 + c0) * sn, sn, nvalid, racc[sl]);
+                        }
+                    }
+                } else {
+                    for (int c0 = half * 32; c0 < p.bn; c0 += 64) {
+                        uint32_t v[32];
+                        tmem_ld32(tb + (uint32_t)c0, v);
+                        const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));   // this tile's columns only
+                        if (mrow && nvalid > 0) {
+                            float x[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+                            emit32<PREC>(p, mo + (long long)(n0 + c0) * sn, sn, nvalid, x);
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
-            ++li;
         }
     }
     __syncthreads();
@@ -457,6 +534,10 @@ __global__ void k_split(SplitSrc s, int rows, int cols, int batch, void* dst, lo
             const __nv_bfloat16 lo = __double2bfloat16(xd - (double)__bfloat162float(hi));
             ((__nv_bfloat16*)dst)[di] = hi;
             ((__nv_bfloat16*)dst)[di + plane] = lo;
+        } else if constexpr (PREC == PPL_PREC_TF32X3) {
+            const float hi = round_tf32((float)xd);
+            ((float*)dst)[di] = hi;
+            ((float*)dst)[di + plane] = round_tf32((float)(xd - (double)hi));
         } else {
             x = (float)xd;
             ((float*)dst)[di] = round_tf32(x);
@@ -465,7 +546,7 @@ __global__ void k_split(SplitSrc s, int rows, int cols, int batch, void* dst, lo
 }
 
 bool make_map(CUtensorMap* m, int prec, const void* ptr, const TcMat& t, int box_rows) {
-    const bool split = (prec == PPL_PREC_BF16X3);
+    const bool split = (prec == PPL_PREC_BF16X3);   // 2-byte elements
     const size_t es = split ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows, (cuuint64_t)(t.batch > 0 ? t.batch : 1)};
     cuuint64_t strides[2] = {(cuuint64_t)(t.ld * es), (cuuint64_t)((t.bstride > 0 ? t.bstride : t.ld * t.rows) * es)};
@@ -506,17 +587,32 @@ int tc_init_driver() {
     g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     static bool attr_done = false;
     if (!attr_done) {
-        if (cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_ATTR) != cudaSuccess ||
-            cudaFuncSetAttribute(k_tc_gemm<PPL_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_ATTR) != cudaSuccess) {
-            cudaGetLastError();
-            return -2;
+        const void* fns[6] = {(const void*)k_tc_gemm<PPL_PREC_BF16X3, false>, (const void*)k_tc_gemm<PPL_PREC_BF16X3, true>,
+                              (const void*)k_tc_gemm<PPL_PREC_TF32, false>,   (const void*)k_tc_gemm<PPL_PREC_TF32, true>,
+                              (const void*)k_tc_gemm<PPL_PREC_TF32X3, false>, (const void*)k_tc_gemm<PPL_PREC_TF32X3, true>};
+        for (const void* f : fns) {
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_ATTR) != cudaSuccess) {
+                cudaGetLastError();
+                return -2;
+            }
         }
         attr_done = true;
     }
     return 0;
 }
+
+namespace {
+
+template <int PREC>
+void launch_tc(bool drain, int grid, size_t smem, cudaStream_t s, const CUtensorMap& a, const CUtensorMap& al,
+               const CUtensorMap& b, const CUtensorMap& bl, const KParams& p) {
+    if (drain)
+        k_tc_gemm<PREC, true><<<grid, 320, smem, s>>>(a, al, b, bl, p);
+    else
+        k_tc_gemm<PREC, false><<<grid, 320, smem, s>>>(a, al, b, bl, p);
+}
+
+}  // namespace
 
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0 || g.K <= 0) return 0;
@@ -528,8 +624,10 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) return -7;
     }
-    const bool split = (g.prec == PPL_PREC_BF16X3);
-    const int KE = split ? 64 : 32;
+    if (g.prec != PPL_PREC_BF16X3 && g.prec != PPL_PREC_TF32 && g.prec != PPL_PREC_TF32X3) return -10;
+    const bool split = (g.prec == PPL_PREC_BF16X3 || g.prec == PPL_PREC_TF32X3);   // hi and lo planes
+    const bool half = (g.prec == PPL_PREC_BF16X3);
+    const int KE = half ? 64 : 32;
     KParams p{};
     p.M = g.M; p.N = g.N; p.K = g.K;
     p.bn = g.bn > 0 ? g.bn : choose_bn(g.N);
@@ -555,10 +653,13 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.ndiv = 1 << 30;
     if (g.out.ndiv > 0 || g.out.sn_hi != 0 || g.out.alpha != 1.0f) return -9;   // columns map by one stride
     p.alpha = 1.0f;
+    p.kchunk = g.kchunk;
+    const bool drain = g.kchunk > 0 && g.kchunk < p.per_split;
+    if (drain && p.bn > 256) return -8;
     p.err = err_flag;
 
     CUtensorMap mAh, mAl, mBh, mBl;
-    const size_t es = split ? 2 : 4;
+    const size_t es = half ? 2 : 4;
     if (!make_map(&mAh, g.prec, g.A.ptr, g.A, TM) || !make_map(&mBh, g.prec, g.B.ptr, g.B, p.bn)) return -3;
     if (split) {
         if (!make_map(&mAl, g.prec, (const char*)g.A.ptr + g.A.plane_elems * es, g.A, TM) ||
@@ -573,10 +674,12 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     const long long tiles = (long long)((g.M + TM - 1) / TM) * ((g.N + p.bn - 1) / p.bn) * g.batch * p.ksplit;
     if (tiles > (1ll << 30)) return -4;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    if (split)
-        k_tc_gemm<PPL_PREC_BF16X3><<<grid, 320, smem, s>>>(mAh, mAl, mBh, mBl, p);
+    if (g.prec == PPL_PREC_BF16X3)
+        launch_tc<PPL_PREC_BF16X3>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
+    else if (g.prec == PPL_PREC_TF32X3)
+        launch_tc<PPL_PREC_TF32X3>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
     else
-        k_tc_gemm<PPL_PREC_TF32><<<grid, 320, smem, s>>>(mAh, mAl, mBh, mBl, p);
+        launch_tc<PPL_PREC_TF32>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
     const cudaError_t le = cudaGetLastError();
     return le == cudaSuccess ? 0 : -(1000 + (int)le);
 }
@@ -595,6 +698,8 @@ void transpose_operand(int prec, const void* src, void* dst, long long plane_ele
     if (prec == PPL_PREC_BF16X3)
         k_transpose<unsigned short, 2><<<grid, block, 0, s>>>((const unsigned short*)src, (unsigned short*)dst,
                                                               plane_elems, n, ld, bstride);
+    else if (prec == PPL_PREC_TF32X3)
+        k_transpose<float, 2><<<grid, block, 0, s>>>((const float*)src, (float*)dst, plane_elems, n, ld, bstride);
     else
         k_transpose<float, 1><<<grid, block, 0, s>>>((const float*)src, (float*)dst, plane_elems, n, ld, bstride);
 }
@@ -605,6 +710,9 @@ void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch
     if (total <= 0) return;
     if (prec == PPL_PREC_BF16X3)
         k_split<PPL_PREC_BF16X3><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,
+                                                                       bstride);
+    else if (prec == PPL_PREC_TF32X3)
+        k_split<PPL_PREC_TF32X3><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,
                                                                        bstride);
     else
         k_split<PPL_PREC_TF32><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,

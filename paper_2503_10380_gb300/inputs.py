@@ -37,7 +37,7 @@ import numpy as np
 
 __all__ = [
     "uniform", "normal", "PplInputs", "make_inputs", "make_factors",
-    "tau_increment", "batch_shapes",
+    "tau_increment", "batch_shapes", "uniform_t", "normal_t", "make_inputs_torch", "tau_increment_t",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -187,8 +187,9 @@ def uniform_t(torch, seed: int, stream: int, count: int, device, start: int = 0)
     return _lsr(torch, x, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
 
 
-def normal_t(torch, seed: int, stream: int, count: int, device):
-    u = uniform_t(torch, seed, stream, 2 * count, device)
+def normal_t(torch, seed: int, stream: int, count: int, device, start: int = 0):
+    """Normals start .. start+count-1 of the stream (normal k uses uniforms 2k, 2k+1)."""
+    u = uniform_t(torch, seed, stream, 2 * count, device, start=2 * start)
     u1, u2 = u[0::2], u[1::2]
     return torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
 
@@ -214,3 +215,19 @@ def make_inputs_torch(o: int, v: int, X: int, R: int, seed: int = 0, device="cud
     t1 = T1_SCALE * normal_t(torch, seed, STREAM_T1, o * v, device).view(o, v)
     tau += t1[:, None, :, None] * t1[None, :, None, :]
     return B.contiguous(), tau, make_factors(seed, o, v, R)
+
+
+def tau_increment_t(torch, tau0_rms: float, shape, k: int, seed: int = 0, device="cuda", chunk: int = 1 << 26):
+    """tau_increment on `device`, given rms(tau_0); the normals are drawn in
+    chunks of `chunk` so that the counter tensors stay small."""
+    n = 1
+    for d in shape:
+        n *= d
+    Z = torch.empty(n, dtype=torch.float64, device=device)
+    for s in range(0, n, chunk):
+        c = min(chunk, n - s)
+        Z[s:s + c] = normal_t(torch, seed, STREAM_TAU_INCREMENT + k, c, device, start=s)
+    Z = Z.view(*shape)
+    out = Z + Z.permute(1, 0, 3, 2)
+    out *= (0.3 ** k) * tau0_rms / math.sqrt(2.0)
+    return out

@@ -11,6 +11,11 @@ Sizes span several tiles and ragged tails.  Tolerances:
   (errors add in quadrature in practice).
 * TF32: operands rounded to nearest with 10 explicit bits, |dx| <= 2^-11 |x|,
   i.e. about 2 * 2^-11 = 1e-3 per product and 4e-3 for the chain; tests use 4e-3.
+* TF32X3: hi = tf32(x), lo = tf32(x - hi), |x - hi - lo| <= 2^-22 |x|; with lo*lo
+  dropped, <= 3 * 2^-22 relative per product; the accumulator is restarted every
+  32 K elements and the chunks are added with round-to-nearest, so the
+  tensor core's round-toward-zero accumulation adds at most one ulp per MMA of
+  one chunk.  Chain bound about 4 * 3 * 2^-22 + 4 * 16 * 2^-23 ~ 1e-5.
 """
 
 import numpy as np
@@ -23,7 +28,7 @@ from paper_2503_10380_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL_MTTKRP = {"fp64": 1e-12, "bf16x3": 1e-4, "tf32": 4e-3}
+TOL_MTTKRP = {"fp64": 1e-12, "bf16x3": 1e-4, "tf32": 4e-3, "tf32x3": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,7 +57,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "tf32x3"])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 600, 200), (37, 130, 1000), (300, 16, 24)])
 def test_tc_gemm_building_block(prec, M, N, K):
     rng = np.random.default_rng(M + N + K)
@@ -61,11 +66,32 @@ def test_tc_gemm_building_block(prec, M, N, K):
     C = binding.tc_gemm(_dev(A), _dev(B), prec).cpu().numpy()
     ref = A.astype(np.float64) @ B.astype(np.float64).T
     bound = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T
-    tol = 3 * 2.0 ** -16 + K * 2.0 ** -24 if prec == "bf16x3" else 2 * 2.0 ** -11 + K * 2.0 ** -24
+    tol = {"bf16x3": 3 * 2.0 ** -16 + K * 2.0 ** -23, "tf32": 2 * 2.0 ** -11 + K * 2.0 ** -23,
+           "tf32x3": 3 * 2.0 ** -22 + K * 2.0 ** -23}[prec]
     assert np.all(np.abs(C - ref) <= tol * bound + 1e-30)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32"])
+def test_restarted_accumulation_has_no_drift():
+    """Operands exact in tf32 and all products positive: every rounding of the
+    sum goes the same way.  The tcgen05 FP32 accumulator rounds toward zero at
+    each MMA, so one accumulator over K = 8192 loses about half an ulp per MMA;
+    TF32X3 restarts it every 32 K elements and adds the chunks with
+    round-to-nearest, so only the few MMAs inside one chunk still round down
+    (about 2e-7 relative here, against about 4e-5 for one accumulator)."""
+    g = torch.Generator().manual_seed(5)
+    M, N, K = 256, 192, 8192
+    A = torch.randint(1024, 2048, (M, K), generator=g).float() / 2048
+    B = torch.randint(1024, 2048, (N, K), generator=g).float() / 2048
+    ref = A.double() @ B.double().T
+    C = binding.tc_gemm(A.cuda(), B.cuda(), "tf32x3").double().cpu()
+    drift = float(((C - ref) * torch.sign(ref)).sum() / ref.abs().sum())
+    assert abs(drift) < 1e-6, drift
+    C1 = binding.tc_gemm(A.cuda(), B.cuda(), "tf32").double().cpu()
+    drift1 = float(((C1 - ref) * torch.sign(ref)).sum() / ref.abs().sum())
+    assert drift1 <= 0.0          # one unrestarted accumulator never rounds up
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32", "tf32x3"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_mttkrp_each_mode(prec, shape):
     o, v, X, R = shape
@@ -75,6 +101,17 @@ def test_mttkrp_each_mode(prec, shape):
         M = cp.mttkrp(m).cpu().numpy()
         ref = orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m)
         assert _rel(M, ref) < TOL_MTTKRP[prec], (m, _rel(M, ref))
+    cp.close()
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[3], (6, 70, 300, 260)])
+def test_restarted_bf16x3_mttkrp(shape):
+    """BF16X3 with the accumulator restarted every K block (acc_chunk = 1)."""
+    o, v, X, R = shape
+    inp = inputs.make_inputs(o, v, X, R, seed=2)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3", acc_chunk=1)
+    for m in orc.MODES:
+        assert _rel(cp.mttkrp(m).cpu().numpy(), orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m)) < TOL_MTTKRP["bf16x3"]
     cp.close()
 
 
@@ -115,7 +152,7 @@ def test_exact_contraction_and_energies(shape):
     cp.close()
 
 
-@pytest.mark.parametrize("prec,kcal_tol", [("bf16x3", 0.1), ("tf32", 0.5)])
+@pytest.mark.parametrize("prec,kcal_tol", [("bf16x3", 0.1), ("tf32", 0.5), ("tf32x3", 0.01)])
 def test_mixed_sweeps_track_fp64_energy(prec, kcal_tol):
     """Config 0: 20 sweeps in mixed precision from the same start as the FP64
     oracle.  BF16X3 keeps the CP energy within 0.1 kcal/mol of the oracle's;
@@ -267,7 +304,7 @@ def test_autotune_picks_a_chunk_and_keeps_results():
     b.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
 def test_dressed_mttkrp_sweeps_and_exact(prec):
     inp = inputs.make_inputs(4, 21, 30, 40, seed=41)
     Bbar = orc.dress(inp.B, inp.t1, inp.o)
@@ -295,7 +332,7 @@ def cp_factors(cp):
     return {k: t.cpu().numpy() for k, t in cp.factors().items()}
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("tf32", 4e-3)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("tf32", 4e-3), ("tf32x3", 1e-5)])
 @pytest.mark.parametrize("dressed", [False, True])
 def test_exact_contraction_on_tensor_cores(prec, tol, dressed):
     inp = inputs.make_inputs(5, 26, 70, 30, seed=44)

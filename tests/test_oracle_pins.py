@@ -359,6 +359,17 @@ def test_torch_generator_matches_numpy_generator():
         assert np.array_equal(f[m], a.factors[m])
 
 
+def test_torch_tau_increment_matches_numpy_across_chunks():
+    torch = pytest.importorskip("torch")
+    a = inputs.make_inputs(3, 5, 4, 2, seed=21)
+    rms = float(np.sqrt(np.mean(a.tau ** 2)))
+    for k in (1, 2):
+        ref = inputs.tau_increment(a.tau, k, seed=21)
+        got = inputs.tau_increment_t(torch, rms, a.tau.shape, k, seed=21, device="cpu", chunk=7)
+        assert np.max(np.abs(got.numpy() - ref)) < 1e-13 * np.max(np.abs(ref))
+        assert np.array_equal(got.numpy(), got.numpy().transpose(1, 0, 3, 2))   # pair symmetry
+
+
 
 # ---------------------------------------------------------------- t1-dressed D-bar
 
