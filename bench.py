@@ -4,10 +4,12 @@
 Workload: one PPL instance with o=20 occupied, v=200 virtual, X=600 auxiliary
 orbitals and CP rank R=800, seeded synthetic inputs shaped like the paper's
 molecules (paper_2503_10380_gb300/inputs.py).  One step = one ALS sweep
-(modes a, b, i, j) with BF16x3 tensor-core MTTKRPs and FP64 Gram / Cholesky
-/ solve / fit.  Prints one JSON line on rank 0.
+(modes a, b, i, j) with TF32x3 tensor-core MTTKRPs (tf32 hi/lo split,
+accumulator restarted every K block) and FP64 Gram / Cholesky / solve / fit.
+BF16x3 is timed beside it with its energy error.  Prints one JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload single|batch|precision|sequence] [--precision bf16x3|tf32|tf32x3]
 
 For N > 1 (one process per GPU under torchrun) every rank runs an
 independent replica (the method has no exchange step on one instance):
@@ -152,6 +154,17 @@ def traffic_from_profile(key: str, src_name: str):
     return None
 
 
+def tensor_peak(pk, precision):
+    """Algorithmic-flop peak of a tensor-core precision: the dtype's sustained
+    rate divided by the MMAs issued per product (three for the split forms)."""
+    bf16 = pk["bf16_tflops_sustained"]
+    tf32 = bf16 * (1.1 / 2.25)          # nominal dense tf32 / bf16 ratio
+    return {"bf16x3": (bf16 / 3.0, "sustained bf16 / 3 (three bf16 MMAs per product)"),
+            "tf32": (tf32, "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25"),
+            "tf32x3": (tf32 / 3.0, "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25, / 3 (three tf32 MMAs "
+                                   "per product)")}[precision]
+
+
 def fp64_solve_flops(o, v, R):
     """Algorithmic FP64 flops of the four mode updates of one sweep: per mode
     2 R^3 / 3 (Cholesky) + 3 dim R^2 (forward and back substitution, Gram)."""
@@ -282,6 +295,25 @@ def run_ours(args, world, rank, local):
     E_f64 = f64.energy()
     f64.close()
 
+    # ---- the other tensor-core precisions on the same start: speed and accuracy
+    variants = {}
+    for prec in ("bf16x3", "tf32x3"):
+        if prec == args.precision:
+            continue
+        alt = binding.CpAls(B, tau, inp.factors, precision=prec, r_chunk=args.r_chunk)
+        alt.set_normR2(normR2)
+        alt.sweep(n_cmp, want_hist=False)
+        E_alt = alt.energy()
+        torch.cuda.synchronize()
+        g0.record(stream)
+        alt.sweep(50, want_hist=False)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        variants[prec] = {"sweeps_per_s": 50 * 1000.0 / g0.elapsed_time(g1), "E_cp": E_alt,
+                          "dE_kcal_per_mol": abs(E_alt - E_f64) * KCAL,
+                          "meets_0.1_kcal": abs(E_alt - E_f64) * KCAL <= 0.1}
+        alt.close()
+
     # ---- end to end through the C ABI with host buffers -----------------------
     # per solve (one CC-like iteration): tau copied from pinned host memory,
     # its operand copies rebuilt, SWEEPS_PER_SOLVE sweeps warm-started from the
@@ -325,17 +357,23 @@ def run_ours(args, world, rank, local):
                          f"threads from {how}"}
 
     pk, pk_kind = peaks()
-    if args.precision == "bf16x3":
-        peak = pk["bf16_tflops_sustained"] / 3.0
-        peak_note = "sustained bf16 / 3 (three bf16 products per BF16x3 product)"
-    else:
-        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
-        peak_note = "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25"
+    peak, peak_note = tensor_peak(pk, args.precision)
     traffic_mttkrp = traffic_from_profile("dram_bytes_per_sweep", "ppl_tc.cu")
     traffic_solve = traffic_from_profile("solve_bytes_per_launch", "ppl_solve.cu")
     solve_ms = phases["solve_a"] + phases["solve_b"] + phases["solve_ij"]
     solve_tflops = fp64_solve_flops(O, V, RANK) / (solve_ms / 1000.0) / 1e12
     fp64_peak = fp64_peak_tflops(pk)
+    roof_solve = {"bound": "alu", "achieved": solve_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                  "frac": solve_tflops / fp64_peak, "traffic": traffic_solve, "ms_per_sweep": solve_ms,
+                  "kernel": "k_solve (FP64 mode updates, cooperative, 4 launches per sweep)",
+                  "peak_source": "derived: 2 DFMA/clk/SM (ncu peak_sustained) x 2 flops x SMs x max SM clock",
+                  "work": "per sweep 4 x 2R^3/3 + 3 R^2 (2v + 2o) FP64 flops"}
+    roof_mttkrp = {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak, "unit": "TFLOP/s",
+                   "frac": mttkrp_tflops / peak, "traffic": traffic_mttkrp, "ms_per_sweep": mttkrp_ms,
+                   "kernel": "k_tc_gemm and its helpers (all MTTKRP contractions of one sweep)",
+                   "peak_source": f"{pk_kind}: {peak_note}",
+                   "work": "per sweep 4 o^2 v^2 R + 16 X v^2 R algorithmic flops"}
+    dominant = roof_mttkrp if mttkrp_ms >= solve_ms else roof_solve
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -347,20 +385,16 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mttkrp_tflops": mttkrp_tflops,
         "phase_ms": phases,
-        "roofline": {"bound": "alu", "achieved": solve_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": solve_tflops / fp64_peak, "traffic": traffic_solve,
-                     "kernel": "k_solve (FP64 mode updates, the dominant kernel: 4 launches per sweep)",
-                     "peak_source": "derived: 2 DFMA/clk/SM (ncu peak_sustained) x 2 flops x SMs x max SM clock",
-                     "work": "per sweep 4 x 2R^3/3 + 3 R^2 (2v + 2o) FP64 flops"},
-        "roofline_mttkrp": {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak, "unit": "TFLOP/s",
-                            "frac": mttkrp_tflops / peak, "traffic": traffic_mttkrp,
-                            "kernel": "k_tc_gemm and its helpers (all MTTKRP contractions of one sweep)",
-                            "peak_source": f"{pk_kind}: {peak_note}",
-                            "work": "per sweep 4 o^2 v^2 R + 16 X v^2 R algorithmic flops"},
+        "roofline": dominant,
+        "roofline_mttkrp": roof_mttkrp,
+        "roofline_solve": roof_solve,
+        "precision_variants": variants,
         "fp64_gpu": {"ms_per_sweep": f64_ms, "sweeps_per_s": 1000.0 / f64_ms,
                      "speedup_mixed_vs_fp64": value / world / (1000.0 / f64_ms)},
         "accuracy": {"sweeps": n_cmp, "E_cp_mixed": E_mixed, "E_cp_fp64": E_f64,
-                     "dE_kcal_per_mol": abs(E_mixed - E_f64) * KCAL, "E_exact": E_exact,
+                     "dE_kcal_per_mol": abs(E_mixed - E_f64) * KCAL,
+                     "dE_rel": abs(E_mixed - E_f64) / abs(E_f64),
+                     "meets_0.1_kcal": abs(E_mixed - E_f64) * KCAL <= 0.1, "E_exact": E_exact,
                      "rank_error_kcal_per_mol": abs(E_f64 - E_exact) * KCAL,
                      "fit_mixed": fits_mixed[-1], "fit_fp64": fits_f64[-1]},
         "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": int(h2d),
@@ -453,7 +487,7 @@ def run_batch(args, world, rank, local):
                "sample": f"one FP64 oracle sweep of each of the first {k} instances, scaled by flops to all 64; "
                          f"threads from {how}"}
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+    peak, _ = tensor_peak(pk, args.precision)
     tflops = flops / (ms / args.steps / 1000.0) / 1e12
     value = world * args.steps / (ms / 1000.0)
     line = {
@@ -498,7 +532,7 @@ def _timed_sweeps(cp, n, stream):
 
 
 def run_precision(args, world, rank, local):
-    """o=40 v=400 X=1200 R=1600: BF16x3 and TF32 against the plain FP64 GPU form
+    """o=40 v=400 X=1200 R=1600: BF16x3, TF32 and TF32x3 against the plain FP64 GPU form
     from the same start after PREC_SWEEPS sweeps (energy in kcal/mol, relative
     error of every factor), and the sweep rate of each form."""
     import numpy as np
@@ -514,8 +548,8 @@ def run_precision(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     o, v, X, R = PREC_CFG
     B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=dev)
-    # ||R||^2 and E_exact from the tensor-core exact contraction (relative error ~1e-5)
-    cp = binding.CpAls(B, tau, fac, precision="bf16x3")
+    # ||R||^2 and E_exact from the TF32x3 tensor-core exact contraction (relative error ~1e-6)
+    cp = binding.CpAls(B, tau, fac, precision="tf32x3")
     normR2, E_exact, _ = cp.exact_contract(mixed=True)
     cp.close()
     del cp
@@ -530,14 +564,14 @@ def run_precision(args, world, rank, local):
     torch.cuda.empty_cache()
     variants = {}
     clocks = None
-    for prec in ("bf16x3", "tf32"):
+    for prec in ("tf32x3", "bf16x3", "tf32"):
         cp = binding.CpAls(B, tau, fac, precision=prec, profile=True)
         cp.set_normR2(normR2)
         cp.sweep(PREC_SWEEPS, want_hist=False)
         E, F, fit = cp.energy(), _factors_host(cp), cp.fit()
         cp.sweep(args.warmup, want_hist=False)
         torch.cuda.synchronize()
-        ck = ClockSampler(local) if prec == "bf16x3" else None
+        ck = ClockSampler(local) if prec == "tf32x3" else None
         ms = _timed_sweeps(cp, args.steps, stream)
         if ck is not None:
             clocks = ck.stop()
@@ -558,25 +592,25 @@ def run_precision(args, world, rank, local):
             "factor_rel_err": {m: float(np.linalg.norm(F[m] - F64[m]) / np.linalg.norm(F64[m])) for m in F64},
             "kernels_per_sweep": launches,
         }
-    ms = reduce_max(variants["bf16x3"]["ms_per_sweep"], world, dev)
+    ms = reduce_max(variants["tf32x3"]["ms_per_sweep"], world, dev)
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"] / 3.0
-    tf = variants["bf16x3"]["mttkrp_tflops"]
+    peak, peak_note = tensor_peak(pk, "tf32x3")
+    tf = variants["tf32x3"]["mttkrp_tflops"]
     line = {
         "metric": METRIC, "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic (seeded; shapes of the paper's molecules)",
+        "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic (seeded; shapes of the paper's molecules)",
         "config": {"workload": f"cp-als-ppl precision study o={o} v={v} X={X} R={R}, {PREC_SWEEPS} sweeps "
                                f"from one start in FP64, BF16x3 and TF32", "o": o, "v": v, "X": X, "R": R,
                    "l2": "inputs larger than L2"},
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                      "traffic": None, "kernel": "all MTTKRP contractions of one sweep (phase events)",
-                     "peak_source": f"{pk_kind}: sustained bf16 / 3"},
+                     "peak_source": f"{pk_kind}: {peak_note}"},
         "fp64_gpu": {"ms_per_sweep": f64_ms, "E_cp": E64, "fit": fit64},
         "variants": variants,
-        "E_exact_bf16x3": E_exact, "normR2_bf16x3": normR2,
+        "E_exact_tf32x3": E_exact, "normR2_tf32x3": normR2,
         "rank_error_kcal_per_mol": abs(E64 - E_exact) * KCAL,
-        "gpu_launches": variants["bf16x3"]["kernels_per_sweep"] * args.steps,
+        "gpu_launches": variants["tf32x3"]["kernels_per_sweep"] * args.steps,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None,
         "cpu_baseline": None,
     }
@@ -624,7 +658,7 @@ def run_sequence(args, world, rank, local):
         steps.append({"k": k, "sweeps": sweeps, "stop": "dfit" if sweeps < SEQ_MAX_SWEEPS else "max_sweeps",
                       "fit": fits[sweeps - 1] if sweeps else None,
                       "dfit_last": abs(fits[sweeps - 1] - fits[sweeps - 2]) if sweeps > 1 else None,
-                      "E_cp": E, "E_exact_bf16x3": E_exact, "solve_s": t2 - t1, "exact_s": t1 - t0})
+                      "E_cp": E, "E_exact_mixed": E_exact, "solve_s": t2 - t1, "exact_s": t1 - t0})
         if rank == 0:
             print(json.dumps({"progress": steps[-1]}), file=sys.stderr, flush=True)
     ck = clocks.stop()
@@ -647,7 +681,7 @@ def run_sequence(args, world, rank, local):
     f64.close()
     t_solve = reduce_max(t_solve, world, dev)
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+    peak, _ = tensor_peak(pk, args.precision)
     tf = alg_flops(o, v, X, R) / (mt_ms / 1000.0) / 1e12
     line = {
         "metric": METRIC, "value": world * n_sweeps / t_solve, "unit": "sweeps/s", "n_gpus": world,
@@ -678,7 +712,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16x3", "tf32"], default="bf16x3")
+    ap.add_argument("--precision", choices=["bf16x3", "tf32", "tf32x3"], default=None,
+                    help="tensor-core precision of the MTTKRP (default: tf32x3, the split that meets the "
+                         "0.1 kcal/mol bar; bf16x3 for --workload batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
     ap.add_argument("--workload", choices=["single", "batch", "precision", "sequence"], default="single",
@@ -686,6 +722,8 @@ def main():
                          "precision: o=40 v=400 X=1200 R=1600 in FP64, BF16x3 and TF32; "
                          "sequence: o=60 v=600 X=1800 R=2400, 15 warm-started CC-like steps")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "bf16x3" if args.workload == "batch" else "tf32x3"
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

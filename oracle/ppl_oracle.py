@@ -9,7 +9,8 @@ Decompositions to Systematically Improve Approximate Tensor-Networks"):
 
 * the DF particle-particle-ladder tensor, Eq. (dfB) with D-bar = D,
       R[a,b,i,j] = sum_{Q,c,d} B[Q,a,c] B[Q,b,d] tau[i,j,c,d],
-  formed explicitly only at tiny sizes;
+  or with the t1-dressed D-bar of Eq. (fulldfB) on the b side, formed
+  explicitly only at tiny sizes;
 * its rank-R CP model, Eq. (cp-ppl): R~[a,b,i,j] = sum_r lam_r Ua[a,r] Ub[b,r] Ui[i,r] Uj[j,r]
   (paper's alpha, beta, gamma, rho; unit-norm columns with the scales in lam,
   The Canonical Polyadic Decomposition section);
