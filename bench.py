@@ -235,6 +235,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     cp = binding.CpAls(B, tau, inp.factors, precision=args.precision, profile=True, r_chunk=args.r_chunk)
+    if not args.r_chunk:
+        args.r_chunk = cp.autotune()       # the library's own r-chunk autotuner (before the timed region)
     normR2, E_exact, _ = cp.exact_contract()
     for _ in range(args.warmup):
         cp.sweep(1, want_hist=False)
@@ -380,7 +382,7 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": args.precision,
         "data": "synthetic (seeded; shapes of the paper's molecules)",
         "config": {"workload": WORKLOAD, "o": O, "v": V, "X": XAUX, "R": RANK,
-                   "precision": args.precision, "r_chunk": args.r_chunk or "auto",
+                   "precision": args.precision, "r_chunk": args.r_chunk,
                    "l2": "inputs larger than L2 (tau, B operand planes ~0.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mttkrp_tflops": mttkrp_tflops,
@@ -566,6 +568,7 @@ def run_precision(args, world, rank, local):
     clocks = None
     for prec in ("tf32x3", "bf16x3", "tf32"):
         cp = binding.CpAls(B, tau, fac, precision=prec, profile=True)
+        rc_chosen = cp.autotune()
         cp.set_normR2(normR2)
         cp.sweep(PREC_SWEEPS, want_hist=False)
         E, F, fit = cp.energy(), _factors_host(cp), cp.fit()
@@ -590,7 +593,7 @@ def run_precision(args, world, rank, local):
             "speedup_vs_fp64_gpu": f64_ms / ms, "E_cp": E, "fit": fit,
             "dE_kcal_per_mol": abs(E - E64) * KCAL, "dE_rel": abs(E - E64) / abs(E64),
             "factor_rel_err": {m: float(np.linalg.norm(F[m] - F64[m]) / np.linalg.norm(F64[m])) for m in F64},
-            "kernels_per_sweep": launches,
+            "kernels_per_sweep": launches, "r_chunk": rc_chosen,
         }
     ms = reduce_max(variants["tf32x3"]["ms_per_sweep"], world, dev)
     pk, pk_kind = peaks()
@@ -638,6 +641,7 @@ def run_sequence(args, world, rank, local):
     rms0 = float(torch.sqrt(torch.mean(tau * tau)))
     torch.cuda.empty_cache()
     cp = binding.CpAls(B, tau, fac, precision=args.precision, profile=True)
+    rc_chosen = cp.autotune()
     clocks = ClockSampler(local)
     steps, t_solve, t_exact, n_sweeps = [], 0.0, 0.0, 0
     for k in range(SEQ_STEPS):
@@ -691,7 +695,7 @@ def run_sequence(args, world, rank, local):
         "config": {"workload": f"cp-als-ppl warm-started CC-like sequence o={o} v={v} X={X} R={R}, {SEQ_STEPS} steps, "
                                f"|dfit| < {SEQ_EPS} or {SEQ_MAX_SWEEPS} sweeps", "o": o, "v": v, "X": X, "R": R,
                    "l2": "inputs larger than L2 (tau 10.4 GB)"},
-        "sweeps_total": n_sweeps, "solve_s": t_solve, "exact_contract_s": t_exact,
+        "sweeps_total": n_sweeps, "solve_s": t_solve, "exact_contract_s": t_exact, "r_chunk": rc_chosen,
         "ms_per_sweep_steady": ms_sweep, "phase_ms": phases,
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                      "traffic": None, "kernel": "all MTTKRP contractions of one sweep (phase events)",

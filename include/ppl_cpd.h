@@ -62,7 +62,10 @@ typedef struct ppl_cpd ppl_cpd;   /* opaque handle, host memory owned by the lib
 
 typedef struct {
     int precision;   /* PPL_PREC_*                                                       */
-    int r_chunk;     /* columns of r processed per pass of the fused chain; 0 = automatic */
+    int r_chunk;     /* columns of r per pass of the chain (workspace grows with it), at most
+                        1024; 0 = automatic: equal chunks of at most 256 columns in FP64,
+                        on the tensor cores as wide as keeps one [rc][X][v] operand
+                        buffer within 2 GiB                                              */
     int use_graph;   /* 1: capture one sweep in a CUDA graph on first use and replay it  */
     int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
     int profile;     /* 1: record CUDA events between the phases of every sweep           */

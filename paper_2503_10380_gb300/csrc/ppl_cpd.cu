@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/ppl_cpd.h"
@@ -46,6 +47,7 @@ struct Layout {
 
 constexpr int NPART = 2 * 304 + 8;
 constexpr int KSMAX = 80;   // most split-K slices of one tensor-core contraction
+constexpr int RC_MAX = 1024; // most rank columns per pass of the chain
 constexpr int NSCAL = 64;
 // scalar slots
 constexpr int SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
@@ -60,15 +62,25 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.ldX = rup(X, 8);
     L.ldo2 = rup((long long)o * o, 8);
     L.ldvv = rup((long long)v * v, 8);
-    // r-chunk: at most 256 columns (one N tile), chunks of equal size
+    // r-chunk: an explicit r_chunk up to RC_MAX; automatic = chunks of equal
+    // size, each at most 256 columns in FP64 and, on the tensor cores, as many
+    // as keep one chunk buffer ([rc][X][v] operand planes) within 2 GiB (fewer
+    // passes re-read the B operand copies fewer times)
     int rc;
     if (op.r_chunk > 0) {
-        rc = op.r_chunk > 256 ? 256 : op.r_chunk;
+        rc = op.r_chunk > RC_MAX ? RC_MAX : op.r_chunk;
     } else {
-        const int nch = (R + 255) / 256;
-        rc = (R + nch - 1) / nch;
+        long long cap = 256;
+        if (tc) {
+            const long long per_r = (long long)X * L.ldv * (op.precision == PPL_PREC_TF32X3 ? 8 : 4);
+            cap = (2ll << 30) / per_r;
+            if (cap > RC_MAX) cap = RC_MAX;
+            if (cap < 16) cap = 16;
+        }
+        const long long nch = (R + cap - 1) / cap;
+        rc = (int)((R + nch - 1) / nch);
     }
-    if (tc) rc = (int)rup(rc, 16) > 256 ? 256 : (int)rup(rc, 16);
+    if (tc) rc = (int)rup(rc, 16) > RC_MAX ? RC_MAX : (int)rup(rc, 16);
     if (rc > R) rc = R;
     L.rc = rc;
     const long long dim = v > o ? v : o;
@@ -488,7 +500,7 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
         TcGemm g1{};
         g1.A = mat(opb(h, (mode == 0 && h->dressed()) ? h->L.BbN : h->L.Bn), pB, X * v, v, 1, ldv, 0);
         g1.B = mat(opb(h, h->L.UopA), pU, R, v, 1, ldv, 0);
-        g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
+        g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
         g1.out = out_split(opb(h, h->L.W), pW, 0, v, ldv, 1, 0, 0, (long long)X * ldv);
         int e = run_tc(h, g1, "W");
         if (e) return e;
@@ -530,7 +542,7 @@ int p_tc(ppl_cpd* h) {
             TcGemm g1{};
             g1.A = mat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.Bp), pB, v * X, v, 1, ldv, 0);
             g1.B = mat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, ldv, 0);
-            g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0;
+            g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
             g1.out = out_split(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, ldX, 1, 0, 0, (long long)v * ldX);
             int e = run_tc(h, g1, "WT");
             if (e) return e;
@@ -1219,13 +1231,22 @@ int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out) {
     if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
     const int planned = h->L.rc;
     const int step = h->tc() ? 16 : 1;
+    // candidates up to the planned (allocated) chunk: fixed widths and the
+    // balanced splits of R into 1..16 passes
     std::vector<int> cand;
     const int base[] = {48, 64, 96, 128, 160, 208, 256};
     for (int c : base) {
         const int cc = (c / step) * step;
         if (cc >= step && cc < planned) cand.push_back(cc);
     }
+    for (int n = 1; n <= 16; ++n) {
+        int cc = (h->R + n - 1) / n;
+        cc = (cc + step - 1) / step * step;
+        if (cc < planned) cand.push_back(cc);
+    }
     cand.push_back(planned);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     int e = enter(h);
     if (e) return e;
     double* M = h->at<double>(h->L.M);

@@ -103,6 +103,7 @@ struct TcGemm {
     int ksplit;             // split-K factor (atomic epilogues only)
     int bn;                 // N tile (multiple of 16, <= 256); 0 = automatic
     int kchunk;             // > 0: restart the accumulator every kchunk K blocks, sum chunks in registers
+    int nfast;              // 1: tile order N-fastest, so that the N tiles of one A row block run together
     TcOut out;
 };
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);

@@ -7,7 +7,9 @@
 //   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol)
 //       with the rows of Z and of Zi appended below V, so the same panel and
 //       trailing updates carry out the forward substitutions Z <- M L^-T and
-//       Zi <- L^-T (only the block rows of Zi that are already non-zero are updated)
+//       Zi <- L^-T (only the block rows of Zi that are already non-zero are updated);
+//       the next diagonal block is updated by three blocks (one lower quarter
+//       each) and factored by block 0 while the others update the rest
 //   P2  U~ = Z L^-1 = Z Zi^T as one product over 16 x 16 output tiles
 //   P3  lam_r = ||U~[:, r]||, U = U~ / lam (a zero column keeps lam = 0)
 //   P4  G = U^T U
@@ -124,6 +126,20 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
 //    substitution (one warp each), then the off-diagonal blocks block-diagonal
 //    by block-diagonal, Li[I][J] = -Li[I][I] (sum_{K=J}^{I-1} L[I][K] Li[K][J]).
 constexpr int SB = 8;   // inverse sub-block
+
+// 1/d for a positive normal d: the PTX approximate reciprocal refined by two
+// Newton-Raphson steps x <- x + x (1 - d x), each squaring the relative error
+// (within an ulp or two of the correctly rounded quotient).  Four FP64 FMAs
+// instead of the longer IEEE division sequence on the factorisation's
+// critical path.
+__device__ __forceinline__ double recip_nr(double d) {
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
 __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* rd, const unsigned short* tri,
                             double (*Tw)[NB + 1], int kb, double tol, unsigned long long* nclamp) {
     const int t = threadIdx.x;
@@ -135,7 +151,7 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
                 atomicAdd(nclamp, 1ull);
             }
             Ls[j][j] = d;
-            rd[j] = 1.0 / d;
+            rd[j] = recip_nr(d);
         }
         __syncthreads();
         const int n = kb - j - 1;
@@ -155,7 +171,7 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
     // L = A_unscaled * diag(1/sqrt(d)), L_jj = sqrt(d_j); rd <- 1 / L_jj
     if (t < kb) {
         const double sd = sqrt(Ls[t][t]);
-        rd[t] = 1.0 / sd;
+        rd[t] = recip_nr(sd);
         Ls[t][t] = sd;
     }
     __syncthreads();
@@ -337,13 +353,63 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         const int ntri = Tk * (Tk + 1) / 2;
         const int nz = ntri + D * Tk;
         const int ntile = nz + (k + 1) * Tk;
+        // With three or more blocks, tile 0 (the next diagonal block) is split:
+        // blocks 0, 1, 2 each update one of its three lower 16 x 16 quarters,
+        // blocks 1 and 2 then signal block 0, which factors the block once both
+        // quarters have landed.  Block 0 takes no other tile.
+        const bool split0 = (G >= 3 && k + 1 < nt && ntile > 0);
+        if (split0 && blockIdx.x < 3) {
+            const int q = blockIdx.x;
+            const int d0 = k0 + kb, nb1 = min(NB, R - d0);
+            const int r0 = (q == 0) ? 0 : 16, c0 = (q == 2) ? 16 : 0;
+            const double* Pd = p.V + (long long)d0 * R + k0;     // rows of the panel at the next block
+            for (int e = tid; e < 16 * NB; e += NT) {
+                const int i = e / NB, s2 = e % NB;
+                Ta[i][s2] = (r0 + i < nb1 && s2 < kb) ? __ldcg(Pd + (long long)(r0 + i) * R + s2) : 0.0;
+                Tb[i][s2] = (c0 + i < nb1 && s2 < kb) ? __ldcg(Pd + (long long)(c0 + i) * R + s2) : 0.0;
+            }
+            __syncthreads();
+            const int ti = tid / 16, tj = tid % 16;
+            double acc = 0.0;
+            for (int s2 = 0; s2 < kb; ++s2) acc = fma(Ta[ti][s2], Tb[tj][s2], acc);
+            const int i = r0 + ti, j = c0 + tj;
+            if (i < nb1 && j <= i) {
+                double* c = p.V + (long long)(d0 + i) * R + d0 + j;
+                *c = __ldcg(c) - acc;
+            }
+            __syncthreads();
+            if (q > 0) {
+                if (tid == 0) atom_add_release(&p.sync[3], 1u);
+            } else {
+                if (tid == 0) {
+                    int ok = 1;
+                    const unsigned int target = 2u * (unsigned int)(k + 1);
+                    const unsigned long long t0 = gtimer();
+                    while (ld_acquire(&p.sync[3]) < target) {
+                        if (ld_vol(&p.sync[2])) {
+                            ok = 0;
+                            break;
+                        }
+                        if (gtimer() - t0 > BAR_NS) {
+                            atomicExch(&p.sync[2], 1u);
+                            atomicOr(p.err, 64u);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                    s_flag = ok;
+                }
+                __syncthreads();
+                if (s_flag) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
+            }
+        }
         int first, stride;
         if (G == 1) {
             first = 0;
             stride = 1;
         } else if (blockIdx.x == 0) {
-            first = 0;
-            stride = ntile + 1;   // tile 0 only
+            first = split0 ? ntile : 0;   // tile 0 only, unless split above
+            stride = ntile + 1;
         } else {
             first = blockIdx.x;
             stride = G - 1;
@@ -405,7 +471,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                     }
                 }
             __syncthreads();
-            if (tile == 0 && k + 1 < nt) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
+            if (tile == 0 && k + 1 < nt && !split0) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
         }
         if (!gsync(p, gen, &s_flag)) return;
     }

@@ -55,6 +55,7 @@ struct KParams {
     int mdiv, ndiv;
     float alpha;
     int kchunk;             // K blocks per accumulation chunk (drained kernels)
+    int nfast;              // 1: consecutive tiles walk N first (one A tile shared by neighbours)
     unsigned int* err;
 };
 
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(320, 1)
             int it = 0;
             for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
                 const int z = t / tiles_mn, rem = t % tiles_mn;
-                const int m0 = (rem % ntm) * TM, n0 = (rem / ntm) * p.bn;
+                const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
                 const int bz = z / p.ksplit, ks = z % p.ksplit;
                 const int kb0 = ks * p.per_split;
                 const int nk = min(p.per_split, p.nkb_total - kb0);
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(320, 1)
         bool ok = true;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const int z = t / tiles_mn, rem = t % tiles_mn;
-            const int m0 = (rem % ntm) * TM, n0 = (rem / ntm) * p.bn;
+            const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
             const int bz = z / p.ksplit, ks = z % p.ksplit;
             const int nk = min(p.per_split, p.nkb_total - ks * p.per_split);
             const int nch = DRAIN ? (nk + p.kchunk - 1) / p.kchunk : 1;
@@ -426,10 +427,23 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                             for (int j = 0; j < 32; ++j)
                                 racc[sl][j] = (c == 0 ? 0.0f : racc[sl][j]) + __uint_as_float(v[j]);
+                        }
+                    }
+                    if (last) {
+                        // the sums are in registers: give the accumulator back to the
+                        // MMA warp before the (long) stores of the tile
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
+#pragma unroll
+                        for (int sl = 0; sl < 4; ++sl) {
+                            const int c0 = half * 32 + sl * 64;
                             const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
-                            if (last && mrow && nvalid > 0)
+                            if (c0 < p.bn && mrow && nvalid > 0)
                                 emit32<PREC>(p, mo + (long long)(n0 + c0) * sn, sn, nvalid, racc[sl]);
                         }
+                        continue;
                     }
                 } else {
                     for (int c0 = half * 32; c0 < p.bn; c0 += 64) {
@@ -654,6 +668,7 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (g.out.ndiv > 0 || g.out.sn_hi != 0 || g.out.alpha != 1.0f) return -9;   // columns map by one stride
     p.alpha = 1.0f;
     p.kchunk = g.kchunk;
+    p.nfast = g.nfast;
     const bool drain = g.kchunk > 0 && g.kchunk < p.per_split;
     if (drain && p.bn > 256) return -8;
     p.err = err_flag;

@@ -347,3 +347,27 @@ def test_exact_contraction_on_tensor_cores(prec, tol, dressed):
     E_ref = orc.energy_of_tensor(R_ref, inp.B, inp.o)
     assert abs(E - E_ref) < 2 * tol * abs(E_ref)
     cp.close()
+
+
+def test_full_size_benchmark_instance():
+    """o=20 v=200 X=600 R=800, the benchmark's instance, in the configuration bench.py
+    times (graph replay, r-chunk from the autotuner): every MTTKRP against the oracle; then,
+    after two sweeps, the library's <R, R~> and ||R~||^2 against the oracle's values
+    of the same quantities evaluated from the library's own factors."""
+    inp = inputs.make_inputs(20, 200, 600, 800, seed=0)
+    refs = {m: orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m) for m in orc.MODES}
+    B, tau = _dev(inp.B), _dev(inp.tau)
+    for prec in ("tf32x3", "bf16x3"):
+        cp = binding.CpAls(B, tau, inp.factors, precision=prec)
+        cp.autotune()
+        for m in orc.MODES:
+            assert _rel(cp.mttkrp(m).cpu().numpy(), refs[m]) < TOL_MTTKRP[prec], (prec, m)
+        cp.sweep(2, want_hist=False)
+        st = cp.stats()
+        f = cp_factors(cp)
+        M_j = orc.mttkrp(inp.Bvv, inp.tau, f, "j")
+        inner = orc.inner_from_mttkrp(M_j, f["j"], f["lam"])
+        norm2 = orc.cp_norm2(f, f["lam"])
+        assert abs(st["last_inner"] - inner) < 4 * TOL_MTTKRP[prec] * abs(inner), (prec, st["last_inner"], inner)
+        assert abs(st["last_norm2"] - norm2) < 1e-10 * norm2, (prec, st["last_norm2"], norm2)
+        cp.close()
