@@ -292,7 +292,7 @@ def test_autotune_picks_a_chunk_and_keeps_results():
     inp = inputs.make_inputs(6, 48, 144, 300, seed=30)
     a = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3")
     rc = a.autotune()
-    assert 16 <= rc <= 256 and rc % 16 == 0
+    assert 16 <= rc <= 1024 and (rc % 16 == 0 or rc == 300)   # a multiple of 16, or all of R
     b = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3")
     a.sweep(2)
     b.sweep(2)
