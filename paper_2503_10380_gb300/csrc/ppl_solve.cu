@@ -4,7 +4,8 @@
 // normalisation; then the new factor's Gram matrix for the next updates).
 //
 //   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, Zi = I, tol = max(2^-52 R max V_kk, 1e-300)
-//   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol)
+//   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol;
+//       panels by warp-per-row triangular solves with the column-scaled diagonal block)
 //       with the rows of Z and of Zi appended below V, so the same panel and
 //       trailing updates carry out the forward substitutions Z <- M L^-T and
 //       Zi <- L^-T (only the block rows of Zi that are already non-zero are updated);
@@ -112,20 +113,16 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
 }
 
 // Factor the kb x kb diagonal block held in Ls (lower) in place, clamping
-// pivots at tol, and form its inverse in Li (lower).  All NT threads.
+// pivots at tol, and leave in Li the column-scaled factor the panel solves
+// with.  All NT threads.
 //
 // GB300 issues an FP64 warp instruction at the same cost whether or not its
-// lanes are masked, so both parts keep the FP64 instruction count close to
-// the useful work:
-//  * factorisation: right-looking on unscaled columns (with d_j the clamped
-//    pivot, A[i][c] -= A[i][j] A[c][j] / d_j, one division per column); at step
-//    j only the n(n+1)/2 active elements of the trailing triangle are
-//    enumerated, packed onto consecutive threads through the (row, col) table
-//    tri; square roots and column scalings follow in one parallel pass;
-//  * inverse: 8 x 8 blocks; the four diagonal blocks are inverted by forward
-//    substitution (one warp each), then the off-diagonal blocks block-diagonal
-//    by block-diagonal, Li[I][J] = -Li[I][I] (sum_{K=J}^{I-1} L[I][K] Li[K][J]).
-constexpr int SB = 8;   // inverse sub-block
+// lanes are masked, so the factorisation keeps the FP64 instruction count close
+// to the useful work: right-looking on unscaled columns (with d_j the clamped
+// pivot, A[i][c] -= A[i][j] A[c][j] / d_j, one reciprocal per column); at step
+// j only the n(n+1)/2 active elements of the trailing triangle are enumerated,
+// packed onto consecutive threads through the (row, col) table tri; square
+// roots and column scalings follow in one parallel pass.
 
 // 1/d for a positive normal d: the PTX approximate reciprocal refined by two
 // Newton-Raphson steps x <- x + x (1 - d x), each squaring the relative error
@@ -141,25 +138,39 @@ __device__ __forceinline__ double recip_nr(double d) {
     return fma(x, e, x);
 }
 __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* rd, const unsigned short* tri,
-                            double (*Tw)[NB + 1], int kb, double tol, unsigned long long* nclamp) {
+                            int kb, double tol, unsigned long long* nclamp) {
     const int t = threadIdx.x;
-    for (int j = 0; j < kb; ++j) {
-        if (t == 0) {
-            double d = Ls[j][j];
-            if (!(d > tol)) {
-                d = tol;
-                atomicAdd(nclamp, 1ull);
-            }
-            Ls[j][j] = d;
-            rd[j] = recip_nr(d);
+    // the pivot of column j is clamped and inverted by thread 0 right after its
+    // own update of that element in step j - 1 (the table puts the next diagonal
+    // element on thread 0), so each step needs one barrier
+    if (t == 0 && kb > 0) {
+        double d = Ls[0][0];
+        if (!(d > tol)) {
+            d = tol;
+            atomicAdd(nclamp, 1ull);
         }
-        __syncthreads();
+        Ls[0][0] = d;
+        rd[0] = recip_nr(d);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
         const int n = kb - j - 1;
         const int nel = n * (n + 1) / 2;
         if (t < nel) {
             const unsigned short ic = tri[t];
             const int ii = j + 1 + (ic >> 8), cc = j + 1 + (ic & 0xff);
-            Ls[ii][cc] = fma(-(Ls[ii][j] * rd[j]), Ls[cc][j], Ls[ii][cc]);
+            const double x = fma(-(Ls[ii][j] * rd[j]), Ls[cc][j], Ls[ii][cc]);
+            if (t == 0) {
+                double d = x;
+                if (!(d > tol)) {
+                    d = tol;
+                    atomicAdd(nclamp, 1ull);
+                }
+                Ls[ii][cc] = d;
+                rd[j + 1] = recip_nr(d);
+            } else {
+                Ls[ii][cc] = x;
+            }
         }
         if (t + NT < nel) {
             const unsigned short ic = tri[t + NT];
@@ -183,57 +194,14 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
             Ls[i][j] *= rd[j];
         }
     }
-    for (int e = t; e < NB * (NB + 1); e += NT) (&Li[0][0])[e] = 0.0;
     __syncthreads();
-    // diagonal 8 x 8 blocks: warp w < 4 inverts block w, lane l < 8 owns column l
-    const int w = t / 32, l = t % 32;
-    if (w < NB / SB && l < SB) {
-        const int o = w * SB, c = o + l;
-        if (c < kb) {
-            double x[SB];
-#pragma unroll
-            for (int i = 0; i < SB; ++i) x[i] = 0.0;
-#pragma unroll
-            for (int i = 0; i < SB; ++i) {
-                if (i >= l && o + i < kb) {
-                    double sacc = (i == l) ? 1.0 : 0.0;
-#pragma unroll
-                    for (int k = 0; k < SB; ++k)
-                        if (k >= l && k < i) sacc = fma(-Ls[o + i][o + k], x[k], sacc);
-                    x[i] = sacc * rd[o + i];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < SB; ++i)
-                if (o + i < kb) Li[o + i][c] = x[i];
-        }
+    // Li <- the column-scaled factor used by the panel's triangular solves:
+    // Li[i][j] = L[i][j] / L[j][j] below the diagonal, Li[i][i] = 1 / L[i][i]
+    for (int e = t; e < NB * NB; e += NT) {
+        const int i = e / NB, j = e % NB;
+        Li[i][j] = (i < kb && j < i) ? Ls[i][j] * rd[j] : ((i < kb && j == i) ? rd[i] : 0.0);
     }
     __syncthreads();
-    // off-diagonal blocks, distance dd = I - J
-    const int nblk = (kb + SB - 1) / SB;
-    for (int dd = 1; dd < nblk; ++dd) {
-        const int npair = nblk - dd;
-        // Tw[I-block rows][J-block cols] = sum_{K=J}^{I-1} L[I][K] Li[K][J]
-        for (int e = t; e < npair * SB * SB; e += NT) {
-            const int pr = e / (SB * SB), r = (e / SB) % SB, cl = e % SB;
-            const int J = pr, I = pr + dd;
-            double acc = 0.0;
-            for (int K = J; K < I; ++K)
-#pragma unroll
-                for (int k = 0; k < SB; ++k) acc = fma(Ls[I * SB + r][K * SB + k], Li[K * SB + k][J * SB + cl], acc);
-            Tw[I * SB + r][J * SB + cl] = acc;
-        }
-        __syncthreads();
-        for (int e = t; e < npair * SB * SB; e += NT) {
-            const int pr = e / (SB * SB), r = (e / SB) % SB, cl = e % SB;
-            const int J = pr, I = pr + dd;
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < SB; ++k) acc = fma(Li[I * SB + r][I * SB + k], Tw[I * SB + k][J * SB + cl], acc);
-            Li[I * SB + r][J * SB + cl] = -acc;
-        }
-        __syncthreads();
-    }
 }
 
 // load the lower kb x kb block of V at (k0, k0) into Ls, factor it, write L
@@ -247,7 +215,7 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
         Ls[i][j] = (i < kb && j <= i) ? __ldcg(p.V + (long long)(k0 + i) * R + k0 + j) : 0.0;
     }
     __syncthreads();
-    diag_factor(Ls, Li, rd, tri, Tw, kb, tol, p.nclamp);
+    diag_factor(Ls, Li, rd, tri, kb, tol, p.nclamp);
     for (int e = tid; e < kb * kb; e += NT) {
         const int i = e / kb, j = e % kb;
         if (j <= i) p.V[(long long)(k0 + i) * R + k0 + j] = Ls[i][j];
@@ -326,6 +294,8 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         // panel: rows below the block (V) and all rows of Z, 8 rows per task
         const int vrows = R - k0 - kb;
         const int prow = vrows + dim + k0 + kb;      // V rows below the block, Z rows, Zi rows of blocks <= k
+        // one warp per row solves x L^T = a: with val_q final, x_q = val_q / L_qq
+        // and val_t -= val_q (L_tq / L_qq), so each column costs one FMA
         const int ntask = (prow + 7) / 8;
         for (int task = blockIdx.x; task < ntask; task += G) {
             const int rr = task * 8 + tid / NB, t = tid % NB;
@@ -336,14 +306,14 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 row = p.Z + (long long)(rr - vrows) * R + k0;
             else if (rr < prow)
                 row = p.Zi + (long long)(rr - vrows - dim) * R + k0;
-            Ta[tid / NB][t] = (row && t < kb) ? __ldcg(row + t) : 0.0;
-            __syncthreads();
-            if (row && t < kb) {
-                double s = 0.0;
-                for (int q = 0; q <= t; ++q) s = fma(Ta[tid / NB][q], Li[t][q], s);
-                row[t] = s;
+            if (row) {   // warp-uniform: rr is the same for the 32 lanes
+                double val = (t < kb) ? __ldcg(row + t) : 0.0;
+                for (int q = 0; q < kb; ++q) {
+                    const double yq = __shfl_sync(0xffffffffu, val, q);
+                    if (t > q) val = fma(-yq, Li[t][q], val);
+                }
+                if (t < kb) row[t] = val * Li[t][t];
             }
-            __syncthreads();
         }
         if (!gsync(p, gen, &s_flag)) return;
         // trailing update of V (lower tiles) and of Z.  Tile 0 is the next
