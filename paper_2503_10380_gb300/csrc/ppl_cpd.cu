@@ -48,6 +48,9 @@ struct Layout {
 constexpr int NPART = 2 * 304 + 8;
 constexpr int KSMAX = 80;   // most split-K slices of one tensor-core contraction
 constexpr int RC_MAX = 1024; // most rank columns per pass of the chain
+#ifndef BATCH_SOLVE_SHARE
+#define BATCH_SOLVE_SHARE 4     // a batched solve takes about SHARE / nstreams of the SMs
+#endif
 constexpr int NSCAL = 64;
 // scalar slots
 constexpr int SC_TERMS = 2, SC_NORMR2 = 8, SC_NORM2_PREV = 9, SC_CROSS = 10, SC_ENERGY = 12,
@@ -197,6 +200,7 @@ struct ppl_cpd {
     bool have_pev;
     long long kernels_per_sweep;
     int guess_policy;
+    int solve_cap;       // > 0: at most this many blocks per cooperative solve (set inside a batch)
     bool cache_valid;
     long long nsolves;
     size_t fac_bytes() const { return (size_t)(2 * v + 2 * o + 1) * R * sizeof(double); }
@@ -323,7 +327,8 @@ int solve_mode(ppl_cpd* h, int m) {
                                   h->at<double>(h->L.V), h->at<double>(h->L.Linv), h->at<double>(h->L.Z),
                                   h->at<double>(h->L.Zi), h->U[m],
                                   h->lam, h->G(m), reinterpret_cast<unsigned int*>(f + 16),
-                                  reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(), h->st);
+                                  reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(),
+                                  h->solve_cap, h->st);
     if (r != 0)
         return fail(h, PPL_ECUDA, "cooperative solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
                     r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
@@ -825,6 +830,7 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     h->have_pev = false;
     h->kernels_per_sweep = 0;
     h->guess_policy = PPL_GUESS_OPTIMAL;
+    h->solve_cap = 0;
     h->cache_valid = false;
     h->nsolves = 0;
     if (op.profile) {
@@ -1343,6 +1349,15 @@ int ppl_cpd_batch_create(ppl_cpd_batch** bp, int n, ppl_cpd* const* handles, int
               cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
     const int ns = nstreams < n ? nstreams : n;
+    // solves are latency-bound chains of small FP64 steps: inside a batch each
+    // takes a share of the SMs so that the solves of several instances overlap
+    if (ns > 1) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int cap = sms > 0 ? (sms * BATCH_SOLVE_SHARE + ns - 1) / ns : 0;
+        for (int k = 0; k < n; ++k) handles[k]->solve_cap = cap;
+    }
     for (int i = 0; ok && i < ns; ++i) {
         cudaStream_t s;
         cudaEvent_t e;
@@ -1446,6 +1461,9 @@ int ppl_cpd_batch_kernels(ppl_cpd_batch* b, long long* kernels_per_sweep) {
 }
 
 int ppl_cpd_batch_destroy(ppl_cpd_batch* b) {
+    if (b)
+        for (ppl_cpd* h : b->hs)
+            if (h) h->solve_cap = 0;
     if (!b) return PPL_OK;
     if (b->origin) cudaStreamSynchronize(b->origin);
     if (b->exec) cudaGraphExecDestroy(b->exec);

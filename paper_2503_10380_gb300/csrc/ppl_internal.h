@@ -35,10 +35,11 @@ void hadamard3(const double* G1, const double* G2, const double* G3, int R, doub
 // One mode update in one cooperative launch (ppl_solve.cu): V = G1.G2.G3, clamped
 // Cholesky, U~ = M V^-1, U = U~ / lam, G = U^T U.  Workspace: V [R][R], Linv
 // [ceil(R/32)][32][32], Z [dim][R], Zi [R][R]; sync (4 words) and maxdiag are reset here.
+// grid_cap > 0 limits the cooperative grid (so that several solves can share the GPU).
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
-                    cudaStream_t s);
+                    int grid_cap, cudaStream_t s);
 // U = Ut / lam (column 2-norms); zero column keeps lam = 0
 void normalise_cols(const double* Ut, int dim, int R, double* U, double* lam, cudaStream_t s);
 // out[0] = sum_{x,r} M[x][r] * Ut[x][r] (Ut = U * lam),  out[1] = lam^T (Ga.Gb.Gi.Gj) lam

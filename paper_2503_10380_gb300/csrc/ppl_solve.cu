@@ -538,7 +538,7 @@ int g_solve_grid = 0;
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
-                    cudaStream_t s) {
+                    int grid_cap, cudaStream_t s) {
     if (g_solve_grid == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
@@ -555,7 +555,8 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
     const int ptask = (R + dim + 7) / 8;
     if (ptask > want) want = ptask;
     if (want < 8) want = 8;
-    const int grid = want < g_solve_grid ? want : g_solve_grid;
+    int grid = want < g_solve_grid ? want : g_solve_grid;
+    if (grid_cap > 0 && grid > grid_cap) grid = grid_cap < 8 ? 8 : grid_cap;
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
     SolveP p;
