@@ -74,7 +74,11 @@ typedef struct {
                         accumulator before the epilogue adds it to FP32 registers with
                         round-to-nearest; 0 = the precision's default (TF32X3: 1,
                         otherwise no restart), -1 = never restart                       */
-    int reserved[9];
+    int acc_steps;   /* > 0 (1..3): restart it every acc_steps MMA K steps (16 bf16 / 8
+                        tf32 columns) inside each K block instead: less round-toward-
+                        zero bias, more round-to-nearest additions, slower; 0 or -1 =
+                        off (the default)                                                */
+    int reserved[8];
 } ppl_cpd_opts;
 
 typedef struct {

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4
 
 class ppl_cpd_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
-                ("profile", c_int), ("dressed", c_int), ("acc_chunk", c_int), ("reserved", c_int * 9)]
+                ("profile", c_int), ("dressed", c_int), ("acc_chunk", c_int), ("acc_steps", c_int), ("reserved", c_int * 8)]
 
 
 class ppl_cpd_stats(ctypes.Structure):
@@ -106,7 +106,7 @@ def _check(rc: int, h=None):
 
 
 def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
-              dressed=False, acc_chunk=0) -> ppl_cpd_opts:
+              dressed=False, acc_chunk=0, acc_steps=0) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -116,6 +116,7 @@ def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, pro
     o.profile = int(bool(profile))
     o.dressed = int(bool(dressed))
     o.acc_chunk = int(acc_chunk)
+    o.acc_steps = int(acc_steps)
     return o
 
 
@@ -304,7 +305,7 @@ class CpAls:
     """
 
     def __init__(self, B, tau, factors, precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False,
-                 profile=False, dressed=False, stream=None, acc_chunk=0):
+                 profile=False, dressed=False, stream=None, acc_chunk=0, acc_steps=0):
         import torch
         self.torch = torch
         X, n, _ = B.shape
@@ -319,7 +320,7 @@ class CpAls:
         parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
         parts.append(torch.ones(R, dtype=torch.float64))
         self.fac = torch.cat(parts).to(dev)
-        self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile, dressed, acc_chunk)
+        self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile, dressed, acc_chunk, acc_steps)
         self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)

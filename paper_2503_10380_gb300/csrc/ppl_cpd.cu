@@ -48,6 +48,9 @@ struct Layout {
 constexpr int NPART = 2 * 304 + 8;
 constexpr int KSMAX = 80;   // most split-K slices of one tensor-core contraction
 constexpr int RC_MAX = 1024; // most rank columns per pass of the chain
+#ifndef TF32X3_ACC_STEPS
+#define TF32X3_ACC_STEPS 0      // default MMA K steps per TF32X3 accumulation chunk (0: a K block)
+#endif
 #ifndef BATCH_SOLVE_SHARE
 #define BATCH_SOLVE_SHARE 4     // a batched solve takes about SHARE / nstreams of the SMs
 #endif
@@ -215,6 +218,12 @@ struct ppl_cpd {
     bool tc() const { return opts.precision != PPL_PREC_FP64; }
     // bytes of one operand element over all its planes
     size_t opbytes() const { return opts.precision == PPL_PREC_TF32X3 ? 8 : 4; }
+    // MMA K steps per accumulation chunk inside a K block (0: whole K blocks)
+    int ksub() const {
+        if (opts.acc_steps > 0) return opts.acc_steps;
+        if (opts.acc_steps < 0) return 0;
+        return opts.precision == PPL_PREC_TF32X3 ? TF32X3_ACC_STEPS : 0;
+    }
     // K blocks per tensor-core accumulation chunk (0: one chunk per tile)
     int kchunk() const {
         if (opts.acc_chunk > 0) return opts.acc_chunk;
@@ -296,6 +305,7 @@ int bn_for(int N) {
 int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
     g.prec = h->opts.precision;
     g.kchunk = h->kchunk();
+    g.ksub = h->ksub();
     if (g.bn == 0) g.bn = bn_for(g.N);
     const int r = tc_gemm(g, h->errflag(), h->st);
     if (r != 0)

@@ -104,6 +104,7 @@ struct TcGemm {
     int ksplit;             // split-K factor (atomic epilogues only)
     int bn;                 // N tile (multiple of 16, <= 256); 0 = automatic
     int kchunk;             // > 0: restart the accumulator every kchunk K blocks, sum chunks in registers
+    int ksub;               // > 0: restart it every ksub MMA K steps inside each K block instead
     int nfast;              // 1: tile order N-fastest, so that the N tiles of one A row block run together
     TcOut out;
 };

@@ -55,6 +55,7 @@ struct KParams {
     int mdiv, ndiv;
     float alpha;
     int kchunk;             // K blocks per accumulation chunk (drained kernels)
+    int ksub;               // > 0: MMA K steps per accumulation chunk, splitting each K block
     int nfast;              // 1: consecutive tiles walk N first (one A tile shared by neighbours)
     unsigned int* err;
 };
@@ -327,6 +328,60 @@ __global__ void __launch_bounds__(320, 1)
                 const int kb0 = ks * p.per_split;
                 const int nk = min(p.per_split, p.nkb_total - kb0);
                 const int kch = DRAIN ? p.kchunk : nk;
+                if (DRAIN && p.ksub > 0) {
+                    // each K block in chunks of ksub MMA K steps, one accumulator each
+                    for (int kbi = 0; kbi < nk && ok; ++kbi, ++it) {
+                        const int s = it % S;
+                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
+                            atomicOr(p.err, 2u);
+                            *vfail = 1;
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = base + stage_bytes * s;
+                        const uint32_t sah = sa, sal = sa + a_bytes;
+                        const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+                        const int kc = (kb0 + kbi) * KE;
+                        int ksteps = KE / KSTEP;
+                        if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+                        const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+                        const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+                        for (int kk0 = 0; kk0 < ksteps; kk0 += p.ksub, ++li) {
+                            const int kk1 = min(ksteps, kk0 + p.ksub);
+                            const int buf = li & 1;
+                            if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
+                                atomicOr(p.err, 8u);
+                                *vfail = 1;
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t d = tmem + (uint32_t)buf * acc_cols;
+                            if constexpr (SPLIT) {
+                                for (int kk = kk0; kk < kk1; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbl + off, idesc, kk > kk0 ? 1u : 0u);
+                                    mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                                }
+                                for (int kk = kk0; kk < kk1; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                                }
+                            } else {
+                                for (int kk = kk0; kk < kk1; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbh + off, idesc, kk > kk0 ? 1u : 0u);
+                                }
+                            }
+                            mma_commit(tfull0 + 8u * buf);
+                        }
+                        if (!ok) break;
+                        mma_commit(empty0 + 8u * s);
+                        s_consumed = it + 1;
+                    }
+                    continue;
+                }
                 for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
                     const int kc1 = min(nk, kc0 + kch);
                     const int buf = li & 1;
@@ -394,7 +449,14 @@ __global__ void __launch_bounds__(320, 1)
             const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
             const int bz = z / p.ksplit, ks = z % p.ksplit;
             const int nk = min(p.per_split, p.nkb_total - ks * p.per_split);
-            const int nch = DRAIN ? (nk + p.kchunk - 1) / p.kchunk : 1;
+            int nch = DRAIN ? (nk + p.kchunk - 1) / p.kchunk : 1;
+            if (DRAIN && p.ksub > 0) {
+                // the same chunking as the MMA warp: ceil(steps / ksub) per K block
+                const int full_st = KE / KSTEP, per_full = (full_st + p.ksub - 1) / p.ksub;
+                const bool tail = (ks * p.per_split + nk == p.nkb_total) && (p.K % KE != 0);
+                nch = (nk - (tail ? 1 : 0)) * per_full;
+                if (tail) nch += (((p.K % KE) + KSTEP - 1) / KSTEP + p.ksub - 1) / p.ksub;
+            }
             const int m = m0 + q * 32 + lane;
             const bool mrow = (m < p.M);
             long long mo = 0;
@@ -668,8 +730,10 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (g.out.ndiv > 0 || g.out.sn_hi != 0 || g.out.alpha != 1.0f) return -9;   // columns map by one stride
     p.alpha = 1.0f;
     p.kchunk = g.kchunk;
+    p.ksub = (g.ksub > 0 && g.ksub < KE / (half ? 16 : 8)) ? g.ksub : 0;
+    if (p.ksub > 0) p.kchunk = 1;
     p.nfast = g.nfast;
-    const bool drain = g.kchunk > 0 && g.kchunk < p.per_split;
+    const bool drain = p.ksub > 0 || (g.kchunk > 0 && g.kchunk < p.per_split);
     if (drain && p.bn > 256) return -8;
     p.err = err_flag;
 

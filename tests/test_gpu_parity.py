@@ -104,14 +104,17 @@ def test_mttkrp_each_mode(prec, shape):
     cp.close()
 
 
+@pytest.mark.parametrize("prec,chunk,steps", [("bf16x3", 1, 0), ("bf16x3", 0, 2), ("tf32x3", 0, 1),
+                                               ("tf32x3", 0, 3), ("tf32x3", 2, -1)])
 @pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[3], (6, 70, 300, 260)])
-def test_restarted_bf16x3_mttkrp(shape):
-    """BF16X3 with the accumulator restarted every K block (acc_chunk = 1)."""
+def test_restarted_accumulation_mttkrp(prec, chunk, steps, shape):
+    """Accumulator restarted every `chunk` K blocks, or every `steps` MMA K steps
+    (a K block split unevenly for steps = 3; K tails at every size here)."""
     o, v, X, R = shape
     inp = inputs.make_inputs(o, v, X, R, seed=2)
-    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision="bf16x3", acc_chunk=1)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec, acc_chunk=chunk, acc_steps=steps)
     for m in orc.MODES:
-        assert _rel(cp.mttkrp(m).cpu().numpy(), orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m)) < TOL_MTTKRP["bf16x3"]
+        assert _rel(cp.mttkrp(m).cpu().numpy(), orc.mttkrp(inp.Bvv, inp.tau, inp.factors, m)) < TOL_MTTKRP[prec]
     cp.close()
 
 
