@@ -223,8 +223,9 @@ typedef struct ppl_cpd_batch ppl_cpd_batch;   /* opaque, host memory owned by th
  * differ) so that one sweep of every instance runs from a single CUDA graph:
  * instance k is issued on internal stream k % nstreams, all forked from and
  * joined back to `stream`.  While in a batch, each handle's cooperative
- * solve uses at most about 4/nstreams of the SMs, so that the latency-bound
- * solves of several instances overlap (reset by ppl_cpd_batch_destroy).  The
+ * solve and each of its tensor-core contractions use at most about
+ * 4/nstreams of the SMs, so that the work of several instances can overlap
+ * (reset by ppl_cpd_batch_destroy).  The
  * handles stay owned by the caller and must outlive the batch. */
 int ppl_cpd_batch_create(ppl_cpd_batch** b, int n, ppl_cpd* const* handles, int nstreams, void* stream);
 

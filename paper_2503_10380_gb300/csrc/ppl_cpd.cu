@@ -51,6 +51,9 @@ constexpr int RC_MAX = 1024; // most rank columns per pass of the chain
 #ifndef TF32X3_ACC_STEPS
 #define TF32X3_ACC_STEPS 0      // default MMA K steps per TF32X3 accumulation chunk (0: a K block)
 #endif
+#ifndef BATCH_TC_SHARE
+#define BATCH_TC_SHARE 4        // a batched tensor-core contraction takes about SHARE / nstreams of the SMs (0: all)
+#endif
 #ifndef BATCH_SOLVE_SHARE
 #define BATCH_SOLVE_SHARE 4     // a batched solve takes about SHARE / nstreams of the SMs
 #endif
@@ -204,6 +207,7 @@ struct ppl_cpd {
     long long kernels_per_sweep;
     int guess_policy;
     int solve_cap;       // > 0: at most this many blocks per cooperative solve (set inside a batch)
+    int tc_cap;          // > 0: at most this many CTAs per tensor-core contraction (set inside a batch)
     bool cache_valid;
     long long nsolves;
     size_t fac_bytes() const { return (size_t)(2 * v + 2 * o + 1) * R * sizeof(double); }
@@ -306,6 +310,7 @@ int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
     g.prec = h->opts.precision;
     g.kchunk = h->kchunk();
     g.ksub = h->ksub();
+    g.grid_cap = h->tc_cap;
     if (g.bn == 0) g.bn = bn_for(g.N);
     const int r = tc_gemm(g, h->errflag(), h->st);
     if (r != 0)
@@ -841,6 +846,7 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     h->kernels_per_sweep = 0;
     h->guess_policy = PPL_GUESS_OPTIMAL;
     h->solve_cap = 0;
+    h->tc_cap = 0;
     h->cache_valid = false;
     h->nsolves = 0;
     if (op.profile) {
@@ -1366,7 +1372,11 @@ int ppl_cpd_batch_create(ppl_cpd_batch** bp, int n, ppl_cpd* const* handles, int
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int cap = sms > 0 ? (sms * BATCH_SOLVE_SHARE + ns - 1) / ns : 0;
-        for (int k = 0; k < n; ++k) handles[k]->solve_cap = cap;
+        const int tcap = sms > 0 ? (sms * BATCH_TC_SHARE + ns - 1) / ns : 0;
+        for (int k = 0; k < n; ++k) {
+            handles[k]->solve_cap = cap;
+            handles[k]->tc_cap = tcap;
+        }
     }
     for (int i = 0; ok && i < ns; ++i) {
         cudaStream_t s;
@@ -1473,7 +1483,10 @@ int ppl_cpd_batch_kernels(ppl_cpd_batch* b, long long* kernels_per_sweep) {
 int ppl_cpd_batch_destroy(ppl_cpd_batch* b) {
     if (b)
         for (ppl_cpd* h : b->hs)
-            if (h) h->solve_cap = 0;
+            if (h) {
+                h->solve_cap = 0;
+                h->tc_cap = 0;
+            }
     if (!b) return PPL_OK;
     if (b->origin) cudaStreamSynchronize(b->origin);
     if (b->exec) cudaGraphExecDestroy(b->exec);

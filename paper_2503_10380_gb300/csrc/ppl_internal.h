@@ -106,6 +106,7 @@ struct TcGemm {
     int kchunk;             // > 0: restart the accumulator every kchunk K blocks, sum chunks in registers
     int ksub;               // > 0: restart it every ksub MMA K steps inside each K block instead
     int nfast;              // 1: tile order N-fastest, so that the N tiles of one A row block run together
+    int grid_cap;           // > 0: at most this many persistent CTAs (several contractions can share the GPU)
     TcOut out;
 };
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);

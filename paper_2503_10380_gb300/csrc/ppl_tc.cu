@@ -752,7 +752,8 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     if (smem > (size_t)SMEM_ATTR) return -6;
     const long long tiles = (long long)((g.M + TM - 1) / TM) * ((g.N + p.bn - 1) / p.bn) * g.batch * p.ksplit;
     if (tiles > (1ll << 30)) return -4;
-    const int grid = (int)(tiles < sms ? tiles : sms);
+    int grid = (int)(tiles < sms ? tiles : sms);
+    if (g.grid_cap > 0 && grid > g.grid_cap) grid = g.grid_cap;
     if (g.prec == PPL_PREC_BF16X3)
         launch_tc<PPL_PREC_BF16X3>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
     else if (g.prec == PPL_PREC_TF32X3)
