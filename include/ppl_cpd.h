@@ -111,8 +111,8 @@ int ppl_cpd_workspace_size(int o, int v, int X, int R, const ppl_cpd_opts* opts,
  *   workspace, ws_bytes: device memory of at least ppl_cpd_workspace_size bytes,
  *            256-byte aligned; owned by the caller, used until ppl_cpd_destroy.
  *   opts     NULL for defaults.
- * The BF16X3/TF32 operand copies of tau and B are made here (device work on
- * `stream`). */
+ * The tensor-core operand copies of tau and B (BF16X3, TF32 or TF32X3) are
+ * made here (device work on `stream`). */
 int ppl_cpd_init(ppl_cpd** h, int o, int v, int X, int R,
                  const double* B, const double* tau, double* factors,
                  void* workspace, size_t ws_bytes, const ppl_cpd_opts* opts, void* stream);
@@ -147,7 +147,7 @@ int ppl_cpd_energy(ppl_cpd* h, double* E_cp);
 int ppl_exact_contract(ppl_cpd* h, double* normR2, double* E_exact, double* R_out);
 
 /* The same exact contraction on the tensor cores, in the handle's precision
- * (BF16X3 or TF32; EINVAL for FP64 handles): per a, G_a[b][(c,d)] =
+ * (BF16X3, TF32 or TF32X3; EINVAL for FP64 handles): per a, G_a[b][(c,d)] =
  * sum_Q B[Q,a,c] D-bar[Q,b,d] and R[a] = G_a tau^T with FP32 accumulation,
  * split-K sums and the ||R||^2 / energy reductions in FP64.  Relative error of
  * the order of the precision's unit roundoff (1e-5 for BF16X3); use

@@ -34,7 +34,8 @@ void kr_build_f64(const double* Ui, const double* Uj, int o, int R, double* KR, 
 void hadamard3(const double* G1, const double* G2, const double* G3, int R, double* V, double* tol, cudaStream_t s);
 // One mode update in one cooperative launch (ppl_solve.cu): V = G1.G2.G3, clamped
 // Cholesky, U~ = M V^-1, U = U~ / lam, G = U^T U.  Workspace: V [R][R], Linv
-// [ceil(R/32)][32][32], Z [dim][R], Zi [R][R]; sync (4 words) and maxdiag are reset here.
+// [ceil(R/32)][32][32] (per diagonal block L[i][j] / L[j][j] below the diagonal and
+// 1 / L[i][i] on it), Z [dim][R], Zi [R][R]; sync (4 words) and maxdiag are reset here.
 // grid_cap > 0 limits the cooperative grid (so that several solves can share the GPU).
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,

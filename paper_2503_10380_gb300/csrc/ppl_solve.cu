@@ -205,7 +205,7 @@ __device__ void diag_factor(double (*Ls)[NB + 1], double (*Li)[NB + 1], double* 
 }
 
 // load the lower kb x kb block of V at (k0, k0) into Ls, factor it, write L
-// back to V and L^-1 to Linv[k]
+// back to V and the column-scaled factor the panels solve with to Linv[k]
 __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB + 1], double (*Li)[NB + 1],
                              double* rd, const unsigned short* tri, double (*Tw)[NB + 1]) {
     const int R = p.R, tid = threadIdx.x;
