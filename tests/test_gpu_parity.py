@@ -374,3 +374,30 @@ def test_full_size_benchmark_instance():
         assert abs(st["last_inner"] - inner) < 4 * TOL_MTTKRP[prec] * abs(inner), (prec, st["last_inner"], inner)
         assert abs(st["last_norm2"] - norm2) < 1e-10 * norm2, (prec, st["last_norm2"], norm2)
         cp.close()
+
+
+@pytest.mark.parametrize("shape", [(40, 400, 1200, 1600), (60, 600, 1800, 2400)])
+def test_full_size_sampled_columns(shape):
+    """The larger configured sizes (o, v, X, R) = (40, 400, 1200, 1600) and
+    (60, 600, 1800, 2400), TF32X3 with the autotuned r-chunk as bench.py runs them:
+    every mode's MTTKRP on six rank columns (first, last, and spread between,
+    so that several r-chunks and the ragged last one are sampled) against the
+    oracle evaluated on those columns alone (column r of an MTTKRP depends only
+    on column r of the factors)."""
+    o, v, X, R = shape
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=5, device="cuda")
+    cp = binding.CpAls(B, tau, fac, precision="tf32x3")
+    cp.autotune()
+    M = {m: cp.mttkrp(m).cpu().numpy() for m in orc.MODES}
+    cp.close()
+    cols = np.unique(np.linspace(0, R - 1, 6).astype(int))
+    Bh = B.cpu().numpy()
+    del B
+    tau_h = tau.cpu().numpy()
+    del tau
+    torch.cuda.empty_cache()
+    Bvv = Bh[:, o:, o:]
+    sub = {m: np.ascontiguousarray(fac[m][:, cols]) for m in orc.MODES}
+    for m in orc.MODES:
+        ref = orc.mttkrp(Bvv, tau_h, sub, m)
+        assert _rel(M[m][:, cols], ref) < TOL_MTTKRP["tf32x3"], (shape, m, _rel(M[m][:, cols], ref))
