@@ -85,6 +85,22 @@ def time_oracle_sweeps(inp, R_s, nsweeps):
     return time.perf_counter() - t0
 
 
+def oracle_estimate(o, v, X, R):
+    """CPU baseline for a size too large to time the oracle on: one FP64 oracle sweep of
+    the o=20 v=200 X=600 R=800 instance is timed on the host cores and its MTTKRP-flop
+    rate is scaled to (o, v, X, R).  Labelled as an estimate."""
+    from paper_2503_10380_gb300 import inputs
+    inp = inputs.make_inputs(O, V, XAUX, RANK, seed=SEED)
+    t = time_oracle_sweeps(inp, RANK, 1)
+    rate = alg_flops(O, V, XAUX, RANK) / t
+    cores, how = oracle_cores()
+    return {"value": rate / alg_flops(o, v, X, R), "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+            "estimate": True,
+            "sample": f"estimate: one FP64 oracle sweep of o={O} v={V} X={XAUX} R={RANK} took {t:.2f} s "
+                      f"({rate / 1e9:.1f} GFLOP/s of MTTKRP flops), scaled by 4o^2v^2R + 16Xv^2R to "
+                      f"o={o} v={v} X={X} R={R}; threads from {how}"}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -624,7 +640,7 @@ def run_precision(args, world, rank, local):
         "rank_error_kcal_per_mol": abs(E64 - E_exact) * KCAL,
         "gpu_launches": variants["tf32x3"]["kernels_per_sweep"] * args.steps,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None,
-        "cpu_baseline": None,
+        "cpu_baseline": oracle_estimate(o, v, X, R) if rank == 0 and world == 1 and not args.no_cpu_baseline else None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -713,7 +729,7 @@ def run_sequence(args, world, rank, local):
         "per_step": steps,
         "gpu_launches": launches * n_sweeps,
         "clocks": {kk: ck[kk] for kk in ("sm_mhz", "sm_max_mhz", "reasons")},
-        "cpu_baseline": None,
+        "cpu_baseline": oracle_estimate(o, v, X, R) if rank == 0 and world == 1 and not args.no_cpu_baseline else None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
