@@ -58,6 +58,27 @@ def test_workspace_grows_with_rank_and_precision_layout(lib):
     assert b16 == t32 and big > b16 and f64 > 0
 
 
+def test_workspace_follows_the_planner_options(lib):
+    ws = binding.ppl_cpd_workspace_size
+    shape = (20, 200, 600, 800)
+    b16 = ws(*shape, binding.make_opts("bf16x3"))
+    t3 = ws(*shape, binding.make_opts("tf32x3"))
+    assert t3 > b16                                   # 8-byte operand elements against 4
+    # explicit r-chunks: more rank columns per pass need wider chunk buffers, capped at 1024
+    sizes = [ws(*shape, binding.make_opts("tf32x3", r_chunk=rc)) for rc in (64, 256, 800)]
+    assert sizes[0] < sizes[1] < sizes[2]
+    big = (20, 200, 600, 3000)
+    assert ws(*big, binding.make_opts("tf32x3", r_chunk=1024)) == ws(*big, binding.make_opts("tf32x3", r_chunk=4096))
+    # automatic chunk: all of R while one [rc][X][v] operand buffer stays within 2 GiB ...
+    assert t3 == ws(*shape, binding.make_opts("tf32x3", r_chunk=800))
+    # ... and equal chunks under that budget otherwise (X v 8 bytes = 8.64 MB per column: 10 x 240)
+    cfg4 = (60, 600, 1800, 2400)
+    assert ws(*cfg4, binding.make_opts("tf32x3")) == ws(*cfg4, binding.make_opts("tf32x3", r_chunk=240))
+    # the dressed D-bar takes room; accumulator restarts take none
+    assert ws(*shape, binding.make_opts("tf32x3", dressed=True)) > t3
+    assert ws(*shape, binding.make_opts("tf32x3", acc_chunk=2, acc_steps=1)) == t3
+
+
 def test_init_rejects_small_workspace_and_null(lib):
     opts = binding.make_opts("fp64")
     need = binding.ppl_cpd_workspace_size(5, 24, 72, 48, opts)
