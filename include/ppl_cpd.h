@@ -93,7 +93,7 @@ typedef struct {
     long long kernels_per_sweep; /* kernel nodes in the captured sweep graph (0 before capture) */
 } ppl_cpd_stats;
 
-/* Fill *opts with defaults: BF16X3, automatic r_chunk, graphs on, eta off. */
+/* Fill *opts with defaults: TF32X3, automatic r_chunk, graphs on, eta off. */
 void ppl_cpd_default_opts(ppl_cpd_opts* opts);
 
 /* Bytes of device workspace a handle with these sizes and options needs.

@@ -105,7 +105,7 @@ def _check(rc: int, h=None):
         raise PplError(rc, msg.decode() if msg else "")
 
 
-def make_opts(precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
+def make_opts(precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
               dressed=False, acc_chunk=0, acc_steps=0) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
@@ -304,7 +304,7 @@ class CpAls:
     workspace; the library does the rest.
     """
 
-    def __init__(self, B, tau, factors, precision="bf16x3", r_chunk=0, use_graph=True, want_eta=False,
+    def __init__(self, B, tau, factors, precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False,
                  profile=False, dressed=False, stream=None, acc_chunk=0, acc_steps=0):
         import torch
         self.torch = torch

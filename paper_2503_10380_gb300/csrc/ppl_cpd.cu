@@ -792,7 +792,7 @@ extern "C" {
 void ppl_cpd_default_opts(ppl_cpd_opts* opts) {
     if (!opts) return;
     memset(opts, 0, sizeof *opts);
-    opts->precision = PPL_PREC_BF16X3;
+    opts->precision = PPL_PREC_TF32X3;
     opts->r_chunk = 0;
     opts->use_graph = 1;
     opts->want_eta = 0;
