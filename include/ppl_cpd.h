@@ -264,9 +264,11 @@ int ppl_cpd_destroy(ppl_cpd* h);
  * PPL_STATIC_SCRATCH_BYTES in the library's device image, which every GPU
  * that loads the library holds until the process exits; it requires
  * 2 * o * R * 8 + 8448 <= PPL_STATIC_SCRATCH_BYTES (o * R <= 523760) and
- * returns PPL_EINVAL otherwise.  The first call on a device looks up the
+ * returns PPL_EINVAL otherwise.  The first call on a device (and the first
+ * call in a new context of it, e.g. after cudaDeviceReset) looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * before any stream capture; a failed call forgets the address.  A launch
+ * error left pending by earlier work is cleared on entry, not reported.  All calls share the one array and it keeps the
  * previous call's contents (the call clears what it accumulates into): calls
  * that overlap on the GPU, from several streams or threads, race. */
 #define PPL_STATIC_SCRATCH_BYTES (8u << 20)

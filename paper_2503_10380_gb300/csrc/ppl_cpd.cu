@@ -33,7 +33,7 @@ struct Layout {
     // offsets (bytes) into the workspace; -1 = absent
     size_t G[4], V, Linv, Z, Zi, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
     size_t T64, W64, Y64, S64;                       // FP64 form
-    size_t tauT, tauN, Bn, Bp, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
+    size_t tauT, tauN, Bn, Bp, BpW, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Bbar, BbN, BbP, BbT;   // t1-dressed D-bar: FP64 [X][v][v] and its operand layouts
     size_t Bq, BbQ, Gop;          // tensor-core exact contraction: B and D-bar as [(p,q)][Q], G_a
     size_t Za, Zb, gov, Gblk, Rblk;
@@ -43,6 +43,8 @@ struct Layout {
     size_t total;
     int rc, na;
     long long ldv, ldX, ldo2, ldvv;
+    long long ldk;   // tensor-core form: v padded to the K-panel width (a K extent of v per block of a compound index)
+    int ke;          // the K-panel width: elements of one 128-byte operand row
 };
 
 constexpr int NPART = 2 * 304 + 8;
@@ -73,8 +75,9 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.ldvv = rup((long long)v * v, 8);
     // r-chunk: an explicit r_chunk up to RC_MAX; automatic = chunks of equal
     // size, each at most 256 columns in FP64 and, on the tensor cores, as many
-    // as keep one chunk buffer ([rc][X][v] operand planes) within 2 GiB (fewer
-    // passes re-read the B operand copies fewer times)
+    // as keep one chunk buffer ([rc][X][v] operand planes) within 8 GiB (each
+    // pass of the chain reads the B operand copies once, so fewer passes move
+    // fewer bytes)
     int rc;
     if (op.r_chunk > 0) {
         rc = op.r_chunk > RC_MAX ? RC_MAX : op.r_chunk;
@@ -82,7 +85,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         long long cap = 256;
         if (tc) {
             const long long per_r = (long long)X * L.ldv * (op.precision == PPL_PREC_TF32X3 ? 8 : 4);
-            cap = (2ll << 30) / per_r;
+            cap = (8ll << 30) / per_r;
             if (cap > RC_MAX) cap = RC_MAX;
             if (cap < 16) cap = 16;
         }
@@ -134,7 +137,9 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.recon = take((size_t)((long long)v * v + (long long)o * o) * L.rcr * d);
     const size_t none = (size_t)-1;
     L.T64 = L.W64 = L.Y64 = L.S64 = none;
-    L.tauT = L.tauN = L.Bn = L.Bp = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
+    L.tauT = L.tauN = L.Bn = L.Bp = L.BpW = L.UopA = L.UopB = L.KRT = L.T = L.Tt = L.W = L.Y = L.WTa = L.WTb = L.S = none;
+    L.ldk = 0;
+    L.ke = 0;
     L.PART = none;
     L.Bbar = L.BbN = L.BbP = L.BbT = none;
     L.Bq = L.BbQ = L.Gop = none;
@@ -145,33 +150,40 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.Y64 = take((size_t)rc * X * v * d);
         L.S64 = take((size_t)rc * v * v * d);
     } else {
+        // operands in the K-panel layout (rows x K, K padded to the panel width ke)
         const size_t e = op.precision == PPL_PREC_TF32X3 ? 8 : 4;   // bf16 hi + lo, fp32 hi + lo, or one fp32
-        L.tauT = take((size_t)v * v * L.ldo2 * e);
-        L.tauN = take((size_t)o * o * L.ldvv * e);
-        L.Bn = take((size_t)X * v * L.ldv * e);
-        L.Bp = take((size_t)v * X * L.ldv * e);
-        L.UopA = take((size_t)R * L.ldv * e);
-        L.UopB = take((size_t)R * L.ldv * e);
-        L.KRT = take((size_t)R * L.ldo2 * e);
-        L.T = take((size_t)R * v * L.ldv * e);
-        L.Tt = take((size_t)R * v * L.ldv * e);
-        L.W = take((size_t)rc * X * L.ldv * e);
-        L.Y = take((size_t)rc * X * L.ldv * e);
-        L.WTa = take((size_t)rc * v * L.ldX * e);
-        L.WTb = take((size_t)rc * v * L.ldX * e);
-        L.S = take((size_t)rc * L.ldvv * e);
+        const long long ke = op.precision == PPL_PREC_BF16X3 ? 64 : 32;
+        L.ke = (int)ke;
+        L.ldk = rup(v, ke);
+        const long long ko2 = rup((long long)o * o, ke), kX = rup(X, ke), kvv = (long long)v * L.ldk;
+        const size_t vv = (size_t)v * v, Xv = (size_t)X * v;
+        L.tauT = take(vv * ko2 * e);                       // rows (c,d), K = (i,j)
+        L.tauN = take((size_t)o * o * kvv * e);            // rows (i,j), K = (c, d) with d padded
+        L.Bn = take(Xv * L.ldk * e);                       // rows (Q,d), K = b
+        L.Bp = take((size_t)v * X * L.ldk * e);            // rows a, K = (Q, c) with c padded
+        L.BpW = take(Xv * L.ldk * e);                      // rows (c,Q), K = a
+        L.UopA = take((size_t)R * L.ldk * e);              // rows r, K = b
+        L.UopB = take((size_t)R * L.ldk * e);
+        L.KRT = take((size_t)R * ko2 * e);                 // rows r, K = (i,j)
+        L.T = take((size_t)R * v * L.ldk * e);             // per r: rows c, K = d
+        L.Tt = take((size_t)R * v * L.ldk * e);            // per r: rows d, K = c
+        L.W = take((size_t)rc * X * L.ldk * e);            // per r: rows Q, K = d
+        L.Y = take((size_t)rc * X * L.ldk * e);            // rows r, K = (Q, c)
+        L.WTa = take((size_t)rc * v * kX * e);             // per r: rows c, K = Q
+        L.WTb = take((size_t)rc * v * kX * e);
+        L.S = take((size_t)rc * kvv * e);                  // rows r, K = (c, d)
         {
             const size_t chain_part = (size_t)KSMAX * (size_t)(v > o * o ? v : o * o) * rc;
             const size_t exact_part = (size_t)KSMAX * (size_t)v * o * o;
             L.PART = take((chain_part > exact_part ? chain_part : exact_part) * sizeof(float));
         }
-        L.Bq = take((size_t)v * v * L.ldX * e);
-        L.Gop = take((size_t)v * L.ldvv * e);
-        if (op.dressed) L.BbQ = take((size_t)v * v * L.ldX * e);
+        L.Bq = take(vv * kX * e);                          // rows (p,q), K = Q
+        L.Gop = take((size_t)v * kvv * e);                 // rows b, K = (c, d)
+        if (op.dressed) L.BbQ = take(vv * kX * e);
         if (op.dressed) {
-            L.BbN = take((size_t)X * v * L.ldv * e);
-            L.BbP = take((size_t)v * X * L.ldv * e);
-            L.BbT = take((size_t)v * X * L.ldv * e);
+            L.BbN = take(Xv * L.ldk * e);
+            L.BbP = take((size_t)v * X * L.ldk * e);
+            L.BbT = take(Xv * L.ldk * e);
         }
     }
     L.total = off;
@@ -261,7 +273,7 @@ int check_cuda(ppl_cpd* h, const char* where) {
 // ---- tensor-core helpers ------------------------------------------------------
 
 TcMat mat(void* p, long long plane, int rows, int cols, int batch, long long ld, long long bstride) {
-    TcMat t;
+    TcMat t{};
     t.ptr = p;
     t.plane_elems = plane;
     t.rows = rows;
@@ -272,28 +284,45 @@ TcMat mat(void* p, long long plane, int rows, int cols, int batch, long long ld,
     return t;
 }
 
-TcOut out_split(void* p, long long plane, long long sb, int mdiv, long long sm_hi, long long sm_lo, int ndiv,
-                long long sn_hi, long long sn_lo) {
+// an operand in the K-panel layout: rows x K, prow rows allocated per panel,
+// batch entries bstride elements apart
+TcMat pmat(void* p, long long plane, int rows, int cols, int batch, long long prow, long long bstride) {
+    TcMat t = mat(p, plane, rows, cols, batch, prow, bstride);
+    t.panel = 1;
+    return t;
+}
+
+// one index of an output map: (panel stride, in-panel stride)
+struct Ix {
+    long long p, s;
+};
+// a plain stride s (the index is not the consumer's K)
+Ix plain(long long s, int ke) { return Ix{ke * s, s}; }
+// the consumer's K index inside its K panels, panels pstride elements apart
+Ix kpan(long long pstride) { return Ix{pstride, 1}; }
+
+// EPI_SPLIT output: element (m, n) of batch b at b*sb + map(m / mdiv, m % mdiv) + map(n)
+TcOut out_map(void* p, long long plane, long long sb, int mdiv, Ix q1, Ix q0, Ix n) {
     TcOut o{};
     o.kind = EPI_SPLIT;
     o.out = p;
     o.plane_elems = plane;
     o.sb = sb;
     o.mdiv = mdiv;
-    o.sm_hi = sm_hi;
-    o.sm_lo = sm_lo;
-    o.ndiv = ndiv;
-    o.sn_hi = sn_hi;
-    o.sn_lo = sn_lo;
+    o.q1p = q1.p; o.q1s = q1.s;
+    o.q0p = q0.p; o.q0s = q0.s;
+    o.np = n.p; o.ns = n.s;
     o.alpha = 1.0f;
     return o;
 }
 
 int auto_ksplit(int M, int N, int bn, int K, int prec) {
+    // split-K slices that fill one wave of the SMs exactly: the work items are
+    // tiles x slices, one per SM
     const int ke = prec == PPL_PREC_BF16X3 ? 64 : 32;
     const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
     const long long nkb = (K + ke - 1) / ke;
-    long long ks = (152 + tiles - 1) / tiles;
+    long long ks = 152 / tiles;
     if (ks > KSMAX) ks = KSMAX;
     if (ks > nkb) ks = nkb;
     if (ks < 1) ks = 1;
@@ -447,38 +476,62 @@ void p_fp64(ppl_cpd* h) {
 
 void* opb(ppl_cpd* h, size_t off) { return h->ws + off; }
 
+// Operand layouts of the tensor-core form (elements per plane; ke = K-panel
+// width, ldk = v padded to ke; a compound K index (Q, c) or (c, d) is
+// Q * ldk + c, so that no panel straddles two blocks and the padding is zero):
+//   tauT   rows (c,d)  K (i,j)         tauN  rows (i,j)  K (c, d)
+//   Bn     rows (Q,d)  K b             Bp    rows a      K (Q, c)      BpW  rows (c,Q)  K a
+//   Uop    rows r      K b             KRT   rows r      K (i,j)
+//   T      per r: rows c, K d          Tt    per r: rows d, K c
+//   W      per r: rows Q, K d          Y     rows r (rc per panel), K (Q, c)
+//   WT     per r: rows c, K Q          S     rows r (rc per panel), K (c, d)
+//   Bq     rows (p,q)  K Q             Gop   rows b      K (c, d)
+struct Pan {
+    long long ke, ldk, kX, ko2, kvv;
+};
+Pan pan_of(const ppl_cpd* h) {
+    Pan q;
+    q.ke = h->L.ke;
+    q.ldk = h->L.ldk;
+    q.kX = rup(h->X, q.ke);
+    q.ko2 = rup((long long)h->o * h->o, q.ke);
+    q.kvv = (long long)h->v * q.ldk;
+    return q;
+}
+
 int uop(ppl_cpd* h, int m, size_t dst) {
     SplitSrc s{};
     s.src = h->U[m];
     s.rmap = ix1(1);
     s.cmap = ix1(h->R);
-    const long long plane = (long long)h->R * h->L.ldv;
-    split_to_operand(h->opts.precision, s, h->R, h->dim(m), 1, opb(h, dst), plane, h->L.ldv, 0, h->st);
+    const long long plane = (long long)h->R * h->L.ldk;
+    split_to_panels(h->opts.precision, s, h->R, h->R, h->dim(m), 0, 0, 1, opb(h, dst), plane, h->st);
     return PPL_OK;
 }
 
 int t_tc(ppl_cpd* h) {
     const int o = h->o, v = h->v, R = h->R;
-    const long long ldv = h->L.ldv, ldo2 = h->L.ldo2;
+    const Pan q = pan_of(h);
     double* KR = h->at<double>(h->L.KR64);
     kr_build_f64(h->U[2], h->U[3], o, R, KR, o * o, h->st);
     SplitSrc s{};
     s.src = KR;
     s.rmap = ix1((long long)o * o);
     s.cmap = ix1(1);
-    const long long pKRT = (long long)R * ldo2;
-    split_to_operand(h->opts.precision, s, R, o * o, 1, opb(h, h->L.KRT), pKRT, ldo2, 0, h->st);
-    const long long pT = (long long)R * v * ldv;
+    const long long pKRT = (long long)R * q.ko2;
+    split_to_panels(h->opts.precision, s, R, R, o * o, 0, 0, 1, opb(h, h->L.KRT), pKRT, h->st);
+    const long long bT = (long long)v * q.ldk;     // one r of T
+    const long long pT = (long long)R * bT;
     TcGemm g{};
-    g.A = mat(opb(h, h->L.tauT), (long long)v * v * ldo2, v * v, o * o, 1, ldo2, 0);
-    g.B = mat(opb(h, h->L.KRT), pKRT, R, o * o, 1, ldo2, 0);
+    g.A = pmat(opb(h, h->L.tauT), (long long)v * v * q.ko2, v * v, o * o, 1, (long long)v * v, 0);
+    g.B = pmat(opb(h, h->L.KRT), pKRT, R, o * o, 1, R, 0);
     g.M = v * v; g.N = R; g.K = o * o; g.batch = 1; g.ksplit = 1;
-    // T[r][c][d]: m = c*v + d
-    g.out = out_split(opb(h, h->L.T), pT, 0, v, ldv, 1, 0, 0, (long long)v * ldv);
+    // T[r]: rows c, K d; m = c*v + d, n = r
+    g.out = out_map(opb(h, h->L.T), pT, 0, v, plain(q.ke, q.ke), kpan((long long)v * q.ke), plain(bT, q.ke));
     int rc = run_tc(h, g, "T");
     if (rc) return rc;
-    // T transposed per r: Tt[r][d][c] = T[r][c][d]
-    transpose_operand(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, v, ldv, (long long)v * ldv, R, h->st);
+    // T transposed per r: Tt[r] rows d, K c
+    transpose_panels(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, v, bT, R, h->st);
     return PPL_OK;
 }
 
@@ -497,8 +550,8 @@ int run_tc_partial(ppl_cpd* h, TcGemm& g, double* out, long long ldo, const char
     g.out.kind = EPI_F32;
     g.out.out = part;
     g.out.sk = (long long)g.M * g.N;
-    g.out.sm_lo = 1;
-    g.out.sn_lo = g.M;
+    g.out.q0p = ke; g.out.q0s = 1;
+    g.out.np = (long long)ke * g.M; g.out.ns = g.M;
     g.out.alpha = 1.0f;
     int e = run_tc(h, g, what);
     if (e) return e;
@@ -508,37 +561,42 @@ int run_tc_partial(ppl_cpd* h, TcGemm& g, double* out, long long ldo, const char
 
 int chain_tc(ppl_cpd* h, int mode, double* Mout) {
     const int v = h->v, X = h->X, R = h->R, rc = h->L.rc;
-    const long long ldv = h->L.ldv;
-    const long long pB = (long long)X * v * ldv;          // Bn / Bp plane
-    const long long pU = (long long)R * ldv;
-    const long long pT = (long long)R * v * ldv;
-    const long long pW = (long long)rc * X * ldv;
+    const Pan q = pan_of(h);
+    const long long pBn = (long long)X * v * q.ldk;       // Bn / Bp plane
+    const long long pU = (long long)R * q.ldk;
+    const long long bT = (long long)v * q.ldk;
+    const long long pT = (long long)R * bT;
+    const long long bW = (long long)X * q.ldk;            // one r of W
+    const long long pW = (long long)rc * bW;
+    const int KY = (int)(X * q.ldk);                      // K of M = B . Y: (Q, c)
     uop(h, mode == 0 ? 1 : 0, h->L.UopA);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
-        // W[r][Q][d] = sum_b B[Q][d][b] U[b][r0+r]
+        // W[r] rows Q, K d: W[r][Q][d] = sum_b B[Q][d][b] U[b][r0+r]
         TcGemm g1{};
-        g1.A = mat(opb(h, (mode == 0 && h->dressed()) ? h->L.BbN : h->L.Bn), pB, X * v, v, 1, ldv, 0);
-        g1.B = mat(opb(h, h->L.UopA), pU, R, v, 1, ldv, 0);
+        g1.A = pmat(opb(h, (mode == 0 && h->dressed()) ? h->L.BbN : h->L.Bn), pBn, X * v, v, 1, (long long)X * v, 0);
+        g1.B = pmat(opb(h, h->L.UopA), pU, R, v, 1, R, 0);
         g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
-        g1.out = out_split(opb(h, h->L.W), pW, 0, v, ldv, 1, 0, 0, (long long)X * ldv);
+        g1.out = out_map(opb(h, h->L.W), pW, 0, v, plain(q.ke, q.ke), kpan((long long)X * q.ke), plain(bW, q.ke));
         int e = run_tc(h, g1, "W");
         if (e) return e;
-        // Y[r][Q][c] = sum_d T[r][c][d] W[r][Q][d]   (mode b: Tt, contracting c)
+        // Y[r][Q][c] = sum_d T[r][c][d] W[r][Q][d]   (mode b: Tt, contracting c);
+        // stored rows r, K (Q, c): m = c, n = Q, batch r
         TcGemm g2{};
-        g2.A = mat(opb(h, mode == 0 ? h->L.T : h->L.Tt), pT, v, v, R, ldv, (long long)v * ldv);
+        g2.A = pmat(opb(h, mode == 0 ? h->L.T : h->L.Tt), pT, v, v, R, v, bT);
         g2.a_b0 = r0; g2.a_bstep = 1;
-        g2.B = mat(opb(h, h->L.W), pW, X, v, rc, ldv, (long long)X * ldv);
+        g2.B = pmat(opb(h, h->L.W), pW, X, v, rc, X, bW);
         g2.b_b0 = 0; g2.b_bstep = 1;
         g2.M = v; g2.N = X; g2.K = v; g2.batch = rcur; g2.ksplit = 1;
-        g2.out = out_split(opb(h, h->L.Y), pW, (long long)X * ldv, 0, 0, 1, 0, 0, ldv);
+        g2.out = out_map(opb(h, h->L.Y), pW, q.ke, 0, Ix{0, 0}, kpan((long long)rc * q.ke),
+                         plain(q.ldk * rc, q.ke));
         e = run_tc(h, g2, "Y");
         if (e) return e;
         // M[a][r0+r] += sum_{Q,c} B[Q][a][c] Y[r][Q][c]
         TcGemm g3{};
-        g3.A = mat(opb(h, (mode == 1 && h->dressed()) ? h->L.BbP : h->L.Bp), pB, v, (int)(X * ldv), 1, X * ldv, 0);
-        g3.B = mat(opb(h, h->L.Y), pW, rc, (int)(X * ldv), 1, X * ldv, 0);
-        g3.M = v; g3.N = rcur; g3.K = (int)(X * ldv); g3.batch = 1;
+        g3.A = pmat(opb(h, (mode == 1 && h->dressed()) ? h->L.BbP : h->L.Bp), pBn, v, KY, 1, v, 0);
+        g3.B = pmat(opb(h, h->L.Y), pW, rcur, KY, 1, rc, 0);
+        g3.M = v; g3.N = rcur; g3.K = KY; g3.batch = 1;
         e = run_tc_partial(h, g3, Mout + r0, R, "M");
         if (e) return e;
     }
@@ -547,44 +605,73 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
 
 int p_tc(ppl_cpd* h) {
     const int o = h->o, v = h->v, X = h->X, R = h->R, rc = h->L.rc;
-    const long long ldv = h->L.ldv, ldX = h->L.ldX, ldvv = h->L.ldvv;
-    const long long pB = (long long)X * v * ldv;
-    const long long pU = (long long)R * ldv;
-    const long long pWT = (long long)rc * v * ldX;
-    const long long pS = (long long)rc * ldvv;
+    const Pan q = pan_of(h);
+    const long long pBn = (long long)X * v * q.ldk;
+    const long long pU = (long long)R * q.ldk;
+    const long long bWT = (long long)v * q.kX;            // one r of WT
+    const long long pWT = (long long)rc * bWT;
+    const long long pS = (long long)rc * q.kvv;
     double* P = h->at<double>(h->L.P);
     uop(h, 0, h->L.UopA);
     uop(h, 1, h->L.UopB);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
         for (int w = 0; w < 2; ++w) {
-            // WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; rows (c,Q) of Bp
+            // WT[r] rows c, K Q: WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; m = c*X + Q, n = r
             TcGemm g1{};
-            g1.A = mat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.Bp), pB, v * X, v, 1, ldv, 0);
-            g1.B = mat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, ldv, 0);
+            g1.A = pmat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.BpW), pBn, v * X, v, 1, (long long)v * X, 0);
+            g1.B = pmat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, R, 0);
             g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
-            g1.out = out_split(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, ldX, 1, 0, 0, (long long)v * ldX);
+            g1.out = out_map(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, plain(q.ke, q.ke),
+                             kpan((long long)v * q.ke), plain(bWT, q.ke));
             int e = run_tc(h, g1, "WT");
             if (e) return e;
         }
-        // S[r][c*v + d] = sum_Q WTa[r][c][Q] WTb[r][d][Q]
+        // S[r][c][d] = sum_Q WTa[r][c][Q] WTb[r][d][Q]; stored rows r, K (c, d): m = d, n = c, batch r
         TcGemm gs{};
-        gs.A = mat(opb(h, h->L.WTb), pWT, v, X, rc, ldX, (long long)v * ldX);
-        gs.B = mat(opb(h, h->L.WTa), pWT, v, X, rc, ldX, (long long)v * ldX);
+        gs.A = pmat(opb(h, h->L.WTb), pWT, v, X, rc, v, bWT);
+        gs.B = pmat(opb(h, h->L.WTa), pWT, v, X, rc, v, bWT);
         gs.a_bstep = 1; gs.b_bstep = 1;
         gs.M = v; gs.N = v; gs.K = X; gs.batch = rcur; gs.ksplit = 1;
-        gs.out = out_split(opb(h, h->L.S), pS, ldvv, 0, 0, 1, 0, 0, v);
+        gs.out = out_map(opb(h, h->L.S), pS, q.ke, 0, Ix{0, 0}, kpan((long long)rc * q.ke), plain(q.ldk * rc, q.ke));
         int e = run_tc(h, gs, "S");
         if (e) return e;
         // P[ij][r0+r] += sum_cd tau[ij][cd] S[r][cd]
         TcGemm gp{};
-        gp.A = mat(opb(h, h->L.tauN), (long long)o * o * ldvv, o * o, v * v, 1, ldvv, 0);
-        gp.B = mat(opb(h, h->L.S), pS, rc, v * v, 1, ldvv, 0);
-        gp.M = o * o; gp.N = rcur; gp.K = v * v; gp.batch = 1;
+        gp.A = pmat(opb(h, h->L.tauN), (long long)o * o * q.kvv, o * o, (int)q.kvv, 1, (long long)o * o, 0);
+        gp.B = pmat(opb(h, h->L.S), pS, rcur, (int)q.kvv, 1, rc, 0);
+        gp.M = o * o; gp.N = rcur; gp.K = (int)q.kvv; gp.batch = 1;
         e = run_tc_partial(h, gp, P + r0, R, "P");
         if (e) return e;
     }
     return PPL_OK;
+}
+
+// the operand copies of a [X][v][v] source (B_vv or D-bar): Bn, Bp, BpW, Bq
+// layouts (see the table above); src is B[Q][p][q] at Q*sQ + p*sp + q
+void split_b_family(ppl_cpd* h, const double* src, long long sQ, long long sp, size_t offN, size_t offP, size_t offW,
+                    size_t offQ) {
+    const int v = h->v, X = h->X, prec = h->opts.precision;
+    const Pan q = pan_of(h);
+    const long long pBn = (long long)X * v * q.ldk;
+    SplitSrc s{};
+    s.src = src;
+    if (offN != (size_t)-1) {   // rows (Q,d), K = b: B[Q][b][d]
+        s.rmap = ix2(v, sQ, 1); s.cmap = ix1(sp);
+        split_to_panels(prec, s, X * v, X * v, v, 0, 0, 1, opb(h, offN), pBn, h->st);
+    }
+    if (offP != (size_t)-1) {   // rows a, K = (Q, c): B[Q][a][c]
+        s.rmap = ix1(sp); s.cmap = ix2((int)q.ldk, sQ, 1);
+        split_to_panels(prec, s, v, v, (int)(X * q.ldk), (int)q.ldk, v, 1, opb(h, offP), pBn, h->st);
+    }
+    if (offW != (size_t)-1) {   // rows (c,Q), K = a: B[Q][c][a]
+        s.rmap = ix2(X, sp, sQ); s.cmap = ix1(1);
+        split_to_panels(prec, s, v * X, v * X, v, 0, 0, 1, opb(h, offW), pBn, h->st);
+    }
+    if (offQ != (size_t)-1) {   // rows (p,q), K = Q: B[Q][p][q]
+        s.rmap = ix2(v, sp, 1); s.cmap = ix1(sQ);
+        split_to_panels(prec, s, v * v, v * v, X, 0, 0, 1, opb(h, offQ), (long long)v * v * q.kX, h->st);
+    }
 }
 
 // D-bar = B_vv - 2 B_vo t1 (t1 == nullptr: D-bar = B_vv), then its operand copies
@@ -601,45 +688,51 @@ void build_dbar(ppl_cpd* h, const double* t1) {
         gemm64(g, h->st);
     }
     if (!h->tc()) return;
-    const int prec = h->opts.precision;
-    const long long ldv = h->L.ldv, pB = (long long)X * v * ldv;
-    SplitSrc s{};
-    s.src = Bb;
-    s.rmap = ix2(v, (long long)v * v, 1); s.cmap = ix1(v);                      // rows (Q,d), K = b
-    split_to_operand(prec, s, X * v, v, 1, opb(h, h->L.BbN), pB, ldv, 0, h->st);
-    s.rmap = ix2(X, v, (long long)v * v); s.cmap = ix1(1);                      // rows (b,Q), K = d
-    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbP), pB, ldv, 0, h->st);
-    s.rmap = ix2(X, 1, (long long)v * v); s.cmap = ix1(v);                      // rows (d,Q), K = b
-    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.BbT), pB, ldv, 0, h->st);
-    s.rmap = ix1(1); s.cmap = ix1((long long)v * v);                             // rows (b,d), K = Q
-    split_to_operand(prec, s, v * v, X, 1, opb(h, h->L.BbQ), (long long)v * v * h->L.ldX, h->L.ldX, 0, h->st);
+    // D-bar[Q][b][d] is not symmetric in (b, d): the b side of every contraction reads it with b as the row index
+    split_b_family(h, Bb, (long long)v * v, v, h->L.BbN, (size_t)-1, (size_t)-1, (size_t)-1);
+    {
+        // rows b, K = (Q, d): D-bar[Q][b][d]
+        const Pan q = pan_of(h);
+        SplitSrc s{};
+        s.src = Bb; s.rmap = ix1(v); s.cmap = ix2((int)q.ldk, (long long)v * v, 1);
+        split_to_panels(h->opts.precision, s, v, v, (int)(X * q.ldk), (int)q.ldk, v, 1, opb(h, h->L.BbP),
+                        (long long)X * v * q.ldk, h->st);
+        // rows (d,Q), K = b: D-bar[Q][b][d]
+        s.rmap = ix2(X, 1, (long long)v * v); s.cmap = ix1(v);
+        split_to_panels(h->opts.precision, s, v * X, v * X, v, 0, 0, 1, opb(h, h->L.BbT), (long long)X * v * q.ldk,
+                        h->st);
+        // rows (b,d), K = Q: D-bar[Q][b][d]
+        s.rmap = ix1(1); s.cmap = ix1((long long)v * v);
+        split_to_panels(h->opts.precision, s, v * v, v * v, X, 0, 0, 1, opb(h, h->L.BbQ), (long long)v * v * q.kX,
+                        h->st);
+    }
 }
 
 // operand copies of tau and B (once per tau / B)
 int prepare_operands(ppl_cpd* h, bool tau_only) {
     if (!h->tc()) return PPL_OK;
     const int o = h->o, v = h->v, X = h->X, n = h->n, prec = h->opts.precision;
-    const long long ldv = h->L.ldv, ldo2 = h->L.ldo2, ldvv = h->L.ldvv;
+    const Pan q = pan_of(h);
     SplitSrc s{};
+    // tauT rows (c,d), K = (i,j)
     s.src = h->tau; s.rmap = ix1(1); s.cmap = ix1((long long)v * v);
-    split_to_operand(prec, s, v * v, o * o, 1, opb(h, h->L.tauT), (long long)v * v * ldo2, ldo2, 0, h->st);
-    s.rmap = ix1((long long)v * v); s.cmap = ix1(1);
-    split_to_operand(prec, s, o * o, v * v, 1, opb(h, h->L.tauN), (long long)o * o * ldvv, ldvv, 0, h->st);
+    split_to_panels(prec, s, v * v, v * v, o * o, 0, 0, 1, opb(h, h->L.tauT), (long long)v * v * q.ko2, h->st);
+    // tauN rows (i,j), K = (c, d), d padded to ldk
+    s.rmap = ix1((long long)v * v); s.cmap = ix2((int)q.ldk, v, 1);
+    split_to_panels(prec, s, o * o, o * o, (int)q.kvv, (int)q.ldk, v, 1, opb(h, h->L.tauN), (long long)o * o * q.kvv,
+                    h->st);
     if (tau_only) return PPL_OK;
-    const long long pB = (long long)X * v * ldv;
-    s.src = h->B + (long long)o * n + o; s.rmap = ix2(v, (long long)n * n, n); s.cmap = ix1(1);
-    split_to_operand(prec, s, X * v, v, 1, opb(h, h->L.Bn), pB, ldv, 0, h->st);
-    s.rmap = ix2(X, n, (long long)n * n);
-    split_to_operand(prec, s, v * X, v, 1, opb(h, h->L.Bp), pB, ldv, 0, h->st);
-    // B as [(p,q)][Q] for the tensor-core exact contraction
-    s.rmap = ix2(v, n, 1); s.cmap = ix1((long long)n * n);
-    split_to_operand(prec, s, v * v, X, 1, opb(h, h->L.Bq), (long long)v * v * h->L.ldX, h->L.ldX, 0, h->st);
-    // scratch whose padding must read as zero
-    zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * ldv * h->opbytes(), h->st);
-    zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * ldvv * h->opbytes(), h->st);
-    zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * ldv * h->opbytes(), h->st);
-    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * h->L.ldX * h->opbytes(), h->st);
-    zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * h->L.ldX * h->opbytes(), h->st);
+    split_b_family(h, h->B + (long long)o * n + o, (long long)n * n, n, h->L.Bn, h->L.Bp, h->L.BpW, h->L.Bq);
+    // intermediates whose K padding (never written by the epilogues) must read as zero
+    const size_t eb = h->opbytes();
+    zero_bytes(opb(h, h->L.T), (size_t)h->R * v * q.ldk * eb, h->st);
+    zero_bytes(opb(h, h->L.Tt), (size_t)h->R * v * q.ldk * eb, h->st);
+    zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * q.ldk * eb, h->st);
+    zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * q.ldk * eb, h->st);
+    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * q.kX * eb, h->st);
+    zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * q.kX * eb, h->st);
+    zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * q.kvv * eb, h->st);
+    zero_bytes(opb(h, h->L.Gop), (size_t)v * q.kvv * eb, h->st);
     return PPL_OK;
 }
 
@@ -1096,7 +1189,7 @@ int ppl_exact_contract_mixed(ppl_cpd* h, double* normR2, double* E_exact, double
     if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
     if (!h->tc()) return fail(h, PPL_EINVAL, "ppl_exact_contract_mixed needs a tensor-core (BF16X3, TF32 or TF32X3) handle");
     const int o = h->o, v = h->v, X = h->X, n = h->n;
-    const long long ldX = h->L.ldX, ldvv = h->L.ldvv, vo2 = (long long)v * o * o;
+    const long long vo2 = (long long)v * o * o;
     int e = enter(h);
     if (e) return e;
     double* gov = h->at<double>(h->L.gov);
@@ -1108,23 +1201,25 @@ int ppl_exact_contract_mixed(ppl_cpd* h, double* normR2, double* E_exact, double
     g.C = gov; g.cm = ix1((long long)o * v); g.cn = ix1(1);
     g.M = o * v; g.N = o * v; g.K = X; g.batch = 1; g.ksplit = 1; g.alpha = 1.0;
     gemm64(g, h->st);
-    const long long pQ = (long long)v * v * ldX, pG = (long long)v * ldvv;
+    const Pan pq = pan_of(h);
+    const long long pQ = (long long)v * v * pq.kX, pG = (long long)v * pq.kvv;
     for (int a = 0; a < v && !e; ++a) {
-        // G_a[b][c*v + d] = sum_Q D-bar[Q][b][d] B[Q][a][c]
+        // G_a[b][c][d] = sum_Q D-bar[Q][b][d] B[Q][a][c]; stored rows b, K (c, d): m = b*v + d, n = c
         TcGemm g1{};
-        g1.A = mat(opb(h, h->dressed() ? h->L.BbQ : h->L.Bq), pQ, v * v, X, 1, ldX, 0);
-        g1.B = mat(opb(h, h->L.Bq), pQ, v, X, v, ldX, (long long)v * ldX);
-        g1.b_b0 = a;
+        g1.A = pmat(opb(h, h->dressed() ? h->L.BbQ : h->L.Bq), pQ, v * v, X, 1, (long long)v * v, 0);
+        g1.B = pmat(opb(h, h->L.Bq), pQ, v * v, X, 1, (long long)v * v, 0);
+        g1.b_row0 = a * v;
         g1.M = v * v; g1.N = v; g1.K = X; g1.batch = 1; g1.ksplit = 1;
-        g1.out = out_split(opb(h, h->L.Gop), pG, 0, v, ldvv, 1, 0, 0, v);
+        g1.out = out_map(opb(h, h->L.Gop), pG, 0, v, plain(pq.ke, pq.ke), kpan((long long)v * pq.ke),
+                         plain(pq.ldk * v, pq.ke));
         e = run_tc(h, g1, "exact G");
         if (e) break;
         // R[a][b][ij] = sum_{cd} G_a[b][cd] tau[ij][cd], split-K summed in FP64
         double* Rdst = R_out ? R_out + (long long)a * vo2 : h->at<double>(h->L.Rblk);
         TcGemm g2{};
-        g2.A = mat(opb(h, h->L.Gop), pG, v, v * v, 1, ldvv, 0);
-        g2.B = mat(opb(h, h->L.tauN), (long long)o * o * ldvv, o * o, v * v, 1, ldvv, 0);
-        g2.M = v; g2.N = o * o; g2.K = v * v; g2.batch = 1;
+        g2.A = pmat(opb(h, h->L.Gop), pG, v, (int)pq.kvv, 1, v, 0);
+        g2.B = pmat(opb(h, h->L.tauN), (long long)o * o * pq.kvv, o * o, (int)pq.kvv, 1, (long long)o * o, 0);
+        g2.M = v; g2.N = o * o; g2.K = (int)pq.kvv; g2.batch = 1;
         e = run_tc_partial(h, g2, Rdst, (long long)o * o, "exact R");
         if (e) break;
         exact_reduce(Rdst, a, 1, v, o, gov, h->at<double>(h->L.partial), acc, h->st);
@@ -1570,7 +1665,12 @@ int ppl_tc_gemm(int precision, int M, int N, int K, const float* A, const float*
     g.M = M; g.N = N; g.K = K; g.batch = 1; g.ksplit = 1;
     g.kchunk = precision == PPL_PREC_TF32X3 ? 1 : 0;
     g.out = TcOut{};
-    g.out.kind = EPI_F32; g.out.out = C; g.out.sm_lo = N; g.out.sn_lo = 1; g.out.alpha = 1.0f;
+    {
+        const int ke = panel_width(precision);
+        g.out.kind = EPI_F32; g.out.out = C; g.out.alpha = 1.0f;
+        g.out.q0p = (long long)ke * N; g.out.q0s = N;    // row m at m * N
+        g.out.np = ke; g.out.ns = 1;                       // column n at n
+    }
     g.bn = bn_for(N);
     int r = tc_gemm(g, flag, s);
     if (r)

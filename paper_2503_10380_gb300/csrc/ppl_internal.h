@@ -81,18 +81,26 @@ struct TcMat {
     long long plane_elems;  // distance to the lo plane in elements (BF16X3)
     int rows, cols;         // cols = K extent; rows = M or N extent
     int batch;              // 3rd dimension
-    long long ld;           // row stride in elements (multiple of 8)
+    long long ld;           // row stride in elements (multiple of 8); panel layout: rows allocated per panel
     long long bstride;      // batch stride in elements (multiple of 8)
+    int panel;              // 1: K-panel layout, element (b, row, k) at
+                            //    b*bstride + (k / KE)*(ld*KE) + row*KE + k % KE, KE = one 128-byte row
+                            //    (32 fp32 or 64 bf16); a panel's elements past K must be zero
 };
-// Epilogue: element (m, n) of batch b goes to
-//   out + b*sb + (m / mdiv)*sm_hi + (m % mdiv)*sm_lo + (n / ndiv)*sn_hi + (n % ndiv)*sn_lo
+// Epilogue: element (m, n) of batch b, split-K slice ks goes to
+//   out + b*sb + ks*sk + rowoff(m) + coloff(n), where with PW the elements of one
+//   128-byte row of the operand precision (32 fp32 or 64 bf16; the K-panel width)
+//   rowoff(m) = (q1 / PW)*q1p + (q1 % PW)*q1s + (q0 / PW)*q0p + (q0 % PW)*q0s,
+//               q1 = m / mdiv, q0 = m % mdiv (mdiv <= 0: q1 = 0, q0 = m)
+//   coloff(n) = (n / PW)*np + (n % PW)*ns
+// so that a plain stride s is (PW*s, s) and a K-panel index is (panel stride, 1).
 enum TcEpi { EPI_SPLIT = 0, EPI_F32 = 1, EPI_ATOMIC_F64 = 2, EPI_ATOMIC_F32 = 3 };
 struct TcOut {
     int kind;               // TcEpi; EPI_SPLIT writes operand planes of the same precision
     void* out; long long plane_elems;
     long long sb, sk;       // batch stride; split-K slice stride (EPI_F32 partials)
-    long long sm_hi, sm_lo, sn_hi, sn_lo;
-    int mdiv, ndiv;
+    int mdiv;
+    long long q1p, q1s, q0p, q0s, np, ns;
     float alpha;
 };
 struct TcGemm {
@@ -124,4 +132,16 @@ struct SplitSrc {
 };
 void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch,
                       void* dst, long long plane_elems, long long ld, long long bstride, cudaStream_t st);
+// The same into the K-panel layout dst[b][c / KE][r][c % KE] (prow rows allocated
+// per panel, npan = ceil(cols / KE) panels per batch entry, bstride = npan*prow*KE);
+// every element of the panels that is not a valid (r < rows, c < cols, and
+// c % kdiv < kmod when kdiv > 0) source element is written as zero.
+void split_to_panels(int prec, const SplitSrc& s, int rows, int prow, int cols, int kdiv, int kmod, int batch,
+                     void* dst, long long plane_elems, cudaStream_t st);
+// Per-r transpose between K-panel layouts: src[b][d / KE][c][d % KE] = T_b[c][d]
+// (n x n, n rows per panel) to dst[b][c / KE][d][c % KE]; bstride elements per b.
+void transpose_panels(int prec, const void* src, void* dst, long long plane_elems, int n, long long bstride,
+                      int batch, cudaStream_t s);
+// elements of one 128-byte operand row (the K-panel width) of a precision
+int panel_width(int prec);
 void zero_bytes(void* p, size_t n, cudaStream_t s);

@@ -24,28 +24,64 @@ constexpr size_t Z_OFFSET = SCALAR_BYTES + PARTIAL_BYTES;
 static __device__ __align__(256) unsigned char g_scratch[PPL_STATIC_SCRATCH_BYTES];
 
 std::mutex g_mu;
-void* g_dev_ptr[64] = {};
+struct Entry {
+    void* ctx;    // the context the address belongs to
+    void* ptr;
+};
+Entry g_dev_ptr[64] = {};
+
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn g_ctx_current = nullptr;
+
+// The current context (the driver's cuCtxGetCurrent, resolved once through the
+// runtime so that the library keeps no link dependency on libcuda); nullptr if
+// it cannot be resolved.
+void* current_context() {
+    if (!g_ctx_current) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_ctx_current = (CtxGetCurrentFn)fn;
+    }
+    void* c = nullptr;
+    return g_ctx_current(&c) == 0 ? c : nullptr;
+}
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the name g_scratch in host code is only a stand-in for the symbol).
-int scratch_address(void** out) {
+// device and context (the name g_scratch in host code is only a stand-in for
+// the symbol).  A context created after a device reset looks it up again.
+int scratch_address(void** out, int* dev_out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         return -1;
     }
+    *dev_out = dev;
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
+    if (!g_dev_ptr[dev].ptr || g_dev_ptr[dev].ctx != ctx || !ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            g_dev_ptr[dev] = Entry{nullptr, nullptr};
             return -2;
         }
-        g_dev_ptr[dev] = p;
+        g_dev_ptr[dev] = Entry{ctx, p};
     }
-    *out = g_dev_ptr[dev];
+    *out = g_dev_ptr[dev].ptr;
     return 0;
+}
+
+// forget the cached address of a device after a failed call
+void drop_address(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_dev_ptr[dev] = Entry{nullptr, nullptr};
 }
 
 int fail_static(int code, const char* msg) {
@@ -68,8 +104,10 @@ extern "C" int ppl_cp_energy_static(int o, int v, int X, int R, const double* B,
                  (long long)o * R, (long long)(room / (2 * sizeof(double))), (size_t)PPL_STATIC_SCRATCH_BYTES);
         return fail_static(PPL_EINVAL, buf);
     }
+    cudaGetLastError();   // a launch error left behind by earlier work is not this call's
     void* base = nullptr;
-    if (scratch_address(&base) != 0)
+    int dev = -1;
+    if (scratch_address(&base, &dev) != 0)
         return fail_static(PPL_ECUDA, "ppl_cp_energy_static: cudaGetSymbolAddress of the scratch array failed");
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)base;
@@ -101,8 +139,11 @@ extern "C" int ppl_cp_energy_static(int o, int v, int X, int R, const double* B,
         sum_partials(chunk, 1, total, 1, s);
     }
     cudaMemcpyAsync(E_cp, total, sizeof(double), cudaMemcpyDeviceToHost, s);
-    const cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    const cudaError_t le = cudaGetLastError();
+    if (e == cudaSuccess) e = le;
+    if (e != cudaSuccess) {
+        drop_address(dev);
         char buf[256];
         snprintf(buf, sizeof buf, "ppl_cp_energy_static: %s", cudaGetErrorString(e));
         return fail_static(PPL_ECUDA, buf);

@@ -51,12 +51,13 @@ struct KParams {
     int batch;
     int kind;
     void* out;
-    long long plane, sb, sk, sm_hi, sm_lo, sn_hi, sn_lo;
-    int mdiv, ndiv;
+    long long plane, sb, sk, q1p, q1s, q0p, q0s, np, ns;
+    int mdiv;
     float alpha;
     int kchunk;             // K blocks per accumulation chunk (drained kernels)
     int ksub;               // > 0: MMA K steps per accumulation chunk, splitting each K block
     int nfast;              // 1: consecutive tiles walk N first (one A tile shared by neighbours)
+    int a_panel, b_panel;   // 1: the operand is in the K-panel layout (4-D tensor map)
     unsigned int* err;
 };
 
@@ -117,6 +118,24 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+// one operand tile: K block kb of rows row.. of batch entry b
+__device__ __forceinline__ void load_op(uint32_t dst, const CUtensorMap* map, bool panel, int kb, int ke, int row, int b,
+                                        uint32_t mbar) {
+    if (panel)
+        tma_load_4d(dst, map, 0, row, kb, b, mbar);
+    else
+        tma_load_3d(dst, map, kb * ke, row, b, mbar);
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ unsigned long long make_desc(uint32_t saddr) {
     unsigned long long d = 0;
@@ -171,48 +190,72 @@ __device__ __forceinline__ float round_tf32(float x) {
     return __uint_as_float(y);
 }
 
-// the epilogue's store of 32 consecutive columns of one row
+// Column offsets of the 32 consecutive columns n0 .. n0 + 31 in the output:
+// (n / PW) * np + (n % PW) * ns.  They span at most two panels (PW >= 32), so
+// column j is at base + j * ns, plus jump once j reaches the next panel.
+struct ColOff {
+    long long base, ns, jump;
+    int split;
+};
 template <int PREC>
-__device__ __forceinline__ void emit32(const KParams& p, long long idx, long long sn, int nvalid, const float (&x)[32]) {
+__device__ __forceinline__ ColOff coloffs(const KParams& p, int n0) {
+    constexpr int PW = Prec<PREC>::KE;
+    ColOff c;
+    c.base = (long long)(n0 / PW) * p.np + (long long)(n0 % PW) * p.ns;
+    c.ns = p.ns;
+    c.jump = p.np - (long long)PW * p.ns;
+    c.split = PW - n0 % PW;
+    return c;
+}
+__device__ __forceinline__ long long col_at(const ColOff& c, int j) {
+    return c.base + (long long)j * c.ns + (j >= c.split ? c.jump : 0ll);
+}
+
+// the epilogue's store of 32 consecutive columns n0 .. n0 + 31 of one row
+template <int PREC>
+__device__ __forceinline__ void emit32(const KParams& p, long long mo, int n0, int nvalid, const float (&x)[32]) {
+    const ColOff co = coloffs<PREC>(p, n0);
     if (p.kind == EPI_SPLIT) {
         if constexpr (PREC == PPL_PREC_BF16X3) {
-            __nv_bfloat16* o = (__nv_bfloat16*)p.out + idx;
+            __nv_bfloat16* o = (__nv_bfloat16*)p.out + mo;
             __nv_bfloat16* ol = o + p.plane;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 if (j < nvalid) {
+                    const long long c = col_at(co, j);
                     const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
-                    o[j * sn] = hi;
-                    ol[j * sn] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+                    o[c] = hi;
+                    ol[c] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
                 }
             }
         } else if constexpr (PREC == PPL_PREC_TF32X3) {
-            float* o = (float*)p.out + idx;
+            float* o = (float*)p.out + mo;
             float* ol = o + p.plane;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 if (j < nvalid) {
+                    const long long c = col_at(co, j);
                     const float hi = round_tf32(x[j]);
-                    o[j * sn] = hi;
-                    ol[j * sn] = round_tf32(x[j] - hi);
+                    o[c] = hi;
+                    ol[c] = round_tf32(x[j] - hi);
                 }
             }
         } else {
-            float* o = (float*)p.out + idx;
+            float* o = (float*)p.out + mo;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (j < nvalid) o[j * sn] = round_tf32(x[j]);
+                if (j < nvalid) o[col_at(co, j)] = round_tf32(x[j]);
         }
     } else if (p.kind == EPI_F32) {
-        float* o = (float*)p.out + idx;
+        float* o = (float*)p.out + mo;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (j < nvalid) o[j * sn] = x[j];
+            if (j < nvalid) o[col_at(co, j)] = x[j];
     } else {
-        double* o = (double*)p.out + idx;
+        double* o = (double*)p.out + mo;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (j < nvalid) atomicAdd(o + j * sn, (double)x[j]);
+            if (j < nvalid) atomicAdd(o + col_at(co, j), (double)x[j]);
     }
 }
 
@@ -304,12 +347,12 @@ __global__ void __launch_bounds__(320, 1)
                     const uint32_t sa = base + stage_bytes * s;
                     const uint32_t fb = full0 + 8u * s;
                     mbar_expect_tx(fb, stage_bytes);
-                    const int kc = (kb0 + kbi) * KE;
-                    tma_load_3d(sa, &mAh, kc, p.a_row0 + m0, a_b, fb);
-                    tma_load_3d(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, kc, p.b_row0 + n0, b_b, fb);
+                    const int kb = kb0 + kbi;
+                    load_op(sa, &mAh, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                    load_op(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
                     if constexpr (SPLIT) {
-                        tma_load_3d(sa + a_bytes, &mAl, kc, p.a_row0 + m0, a_b, fb);
-                        tma_load_3d(sa + 2u * a_bytes + b_bytes, &mBl, kc, p.b_row0 + n0, b_b, fb);
+                        load_op(sa + a_bytes, &mAl, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                        load_op(sa + 2u * a_bytes + b_bytes, &mBl, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
                     }
                     s_issued = it + 1;
                 }
@@ -460,10 +503,12 @@ __global__ void __launch_bounds__(320, 1)
             const int m = m0 + q * 32 + lane;
             const bool mrow = (m < p.M);
             long long mo = 0;
-            if (mrow)
-                mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(m / p.mdiv) * p.sm_hi +
-                     (long long)(m % p.mdiv) * p.sm_lo;
-            const long long sn = p.sn_lo;
+            if (mrow) {
+                constexpr int PW = Prec<PREC>::KE;
+                const int q1 = m / p.mdiv, q0 = m % p.mdiv;
+                mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(q1 / PW) * p.q1p +
+                     (long long)(q1 % PW) * p.q1s + (long long)(q0 / PW) * p.q0p + (long long)(q0 % PW) * p.q0s;
+            }
             for (int c = 0; c < nch; ++c, ++li) {
                 const int buf = li & 1;
                 if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
@@ -502,8 +547,7 @@ __global__ void __launch_bounds__(320, 1)
                         for (int sl = 0; sl < 4; ++sl) {
                             const int c0 = half * 32 + sl * 64;
                             const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
-                            if (c0 < p.bn && mrow && nvalid > 0)
-                                emit32<PREC>(p, mo + (long long)(n0 + c0) * sn, sn, nvalid, racc[sl]);
+                            if (c0 < p.bn && mrow && nvalid > 0) emit32<PREC>(p, mo, n0 + c0, nvalid, racc[sl]);
                         }
                         continue;
                     }
@@ -516,7 +560,7 @@ __global__ void __launch_bounds__(320, 1)
                             float x[32];
 #pragma unroll
                             for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
-                            emit32<PREC>(p, mo + (long long)(n0 + c0) * sn, sn, nvalid, x);
+                            emit32<PREC>(p, mo, n0 + c0, nvalid, x);
                         }
                     }
                 }
@@ -621,17 +665,94 @@ __global__ void k_split(SplitSrc s, int rows, int cols, int batch, void* dst, lo
     }
 }
 
+// FP64 (or FP32) source -> operand planes in the K-panel layout; one thread per
+// destination element, so the writes are contiguous.
+template <int PREC>
+__global__ void k_split_panels(SplitSrc s, int rows, int prow, int cols, int kdiv, int kmod, int npan, int batch,
+                               void* dst, long long plane) {
+    constexpr int KE = Prec<PREC>::KE;
+    const long long per_pan = (long long)prow * KE;
+    const long long per = per_pan * npan;
+    const long long total = per * batch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / per);
+        const long long rem = e % per;
+        const int pan = (int)(rem / per_pan);
+        const int rk = (int)(rem % per_pan);
+        const int r = rk / KE, c = pan * KE + rk % KE;
+        double xd = 0.0;
+        if (r < rows && c < cols && (kdiv <= 0 || c % kdiv < kmod)) {
+            const long long si = (long long)b * s.bstride + ixd(s.rmap, r) + ixd(s.cmap, c);
+            xd = s.src32 ? (double)s.src32[si] : s.src[si];
+        }
+        if constexpr (PREC == PPL_PREC_BF16X3) {
+            const __nv_bfloat16 hi = __double2bfloat16(xd);
+            ((__nv_bfloat16*)dst)[e] = hi;
+            ((__nv_bfloat16*)dst)[e + plane] = __double2bfloat16(xd - (double)__bfloat162float(hi));
+        } else if constexpr (PREC == PPL_PREC_TF32X3) {
+            const float hi = round_tf32((float)xd);
+            ((float*)dst)[e] = hi;
+            ((float*)dst)[e + plane] = round_tf32((float)(xd - (double)hi));
+        } else {
+            ((float*)dst)[e] = round_tf32((float)xd);
+        }
+    }
+}
+
+// T_b[c][d] in [b][d / KE][c][d % KE] -> [b][c / KE][d][c % KE] (n rows per panel),
+// through a KE x KE tile in shared memory: both sides read and write whole
+// contiguous KE x KE blocks.
+template <typename T, int PLANES, int KE>
+__global__ void k_transpose_panels(const T* src, T* dst, long long plane, int n, long long bstride) {
+    __shared__ T tile[PLANES][KE][KE + 1];
+    const int b = blockIdx.z;
+    const int c0 = blockIdx.y * KE, d0 = blockIdx.x * KE;    // this block: c in [c0, c0+KE), d in [d0, d0+KE)
+    if (c0 >= n || d0 >= n) return;
+    const long long off = (long long)b * bstride;
+    const long long pan = (long long)n * KE;
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int ci = e / KE, di = e % KE;          // reads: d fastest
+        const int c = c0 + ci, d = d0 + di;
+        for (int pl = 0; pl < PLANES; ++pl)
+            tile[pl][ci][di] = (c < n && d < n) ? src[pl * plane + off + (long long)(d / KE) * pan + (long long)c * KE + d % KE]
+                                                : T(0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int di = e / KE, ci = e % KE;          // writes: c fastest
+        const int c = c0 + ci, d = d0 + di;
+        if (c < n && d < n)
+            for (int pl = 0; pl < PLANES; ++pl)
+                dst[pl * plane + off + (long long)(c / KE) * pan + (long long)d * KE + c % KE] = tile[pl][ci][di];
+    }
+}
+
 bool make_map(CUtensorMap* m, int prec, const void* ptr, const TcMat& t, int box_rows) {
     const bool split = (prec == PPL_PREC_BF16X3);   // 2-byte elements
     const size_t es = split ? 2 : 4;
-    cuuint64_t dims[3] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows, (cuuint64_t)(t.batch > 0 ? t.batch : 1)};
-    cuuint64_t strides[2] = {(cuuint64_t)(t.ld * es), (cuuint64_t)((t.bstride > 0 ? t.bstride : t.ld * t.rows) * es)};
-    cuuint32_t box[3] = {(cuuint32_t)(KROW_BYTES / es), (cuuint32_t)box_rows, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(m, split ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                          const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t ke = KROW_BYTES / es;
+    const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t nb = (cuuint64_t)(t.batch > 0 ? t.batch : 1);
+    CUresult r;
+    if (t.panel) {
+        // K panels of ke elements: {k in panel, row, panel, batch}
+        const cuuint64_t npan = ((cuuint64_t)t.cols + ke - 1) / ke;
+        cuuint64_t dims[4] = {ke, (cuuint64_t)t.rows, npan, nb};
+        const cuuint64_t bs = (cuuint64_t)(t.bstride > 0 ? t.bstride : (long long)npan * t.ld * (long long)ke);
+        cuuint64_t strides[3] = {ke * es, (cuuint64_t)t.ld * ke * es, bs * es};
+        cuuint32_t box[4] = {(cuuint32_t)ke, (cuuint32_t)box_rows, 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        r = g_encode(m, dt, 4, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[3] = {(cuuint64_t)t.cols, (cuuint64_t)t.rows, nb};
+        cuuint64_t strides[2] = {(cuuint64_t)(t.ld * es), (cuuint64_t)((t.bstride > 0 ? t.bstride : t.ld * t.rows) * es)};
+        cuuint32_t box[3] = {(cuuint32_t)ke, (cuuint32_t)box_rows, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        r = g_encode(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     return r == CUDA_SUCCESS;
 }
 
@@ -724,15 +845,16 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.batch = g.batch;
     p.kind = g.out.kind; p.out = g.out.out; p.plane = g.out.plane_elems;
     p.sb = g.out.sb; p.sk = g.out.sk;
-    p.sm_hi = g.out.sm_hi; p.sm_lo = g.out.sm_lo; p.sn_hi = g.out.sn_hi; p.sn_lo = g.out.sn_lo;
+    p.q1p = g.out.q1p; p.q1s = g.out.q1s; p.q0p = g.out.q0p; p.q0s = g.out.q0s; p.np = g.out.np; p.ns = g.out.ns;
     p.mdiv = g.out.mdiv > 0 ? g.out.mdiv : (1 << 30);
-    p.ndiv = 1 << 30;
-    if (g.out.ndiv > 0 || g.out.sn_hi != 0 || g.out.alpha != 1.0f) return -9;   // columns map by one stride
+    if (g.out.alpha != 1.0f) return -9;
     p.alpha = 1.0f;
     p.kchunk = g.kchunk;
     p.ksub = (g.ksub > 0 && g.ksub < KE / (half ? 16 : 8)) ? g.ksub : 0;
     if (p.ksub > 0) p.kchunk = 1;
     p.nfast = g.nfast;
+    p.a_panel = g.A.panel ? 1 : 0;
+    p.b_panel = g.B.panel ? 1 : 0;
     const bool drain = p.ksub > 0 || (g.kchunk > 0 && g.kchunk < p.per_split);
     if (drain && p.bn > 256) return -8;
     p.err = err_flag;
@@ -797,6 +919,43 @@ void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch
     else
         k_split<PPL_PREC_TF32><<<grid_for(total, 256), 256, 0, st>>>(s, rows, cols, batch, dst, plane_elems, ld,
                                                                      bstride);
+}
+
+int panel_width(int prec) { return prec == PPL_PREC_BF16X3 ? 64 : 32; }
+
+void split_to_panels(int prec, const SplitSrc& s, int rows, int prow, int cols, int kdiv, int kmod, int batch,
+                     void* dst, long long plane_elems, cudaStream_t st) {
+    const int ke = panel_width(prec);
+    const int npan = (cols + ke - 1) / ke;
+    const long long total = (long long)prow * ke * npan * batch;
+    if (total <= 0) return;
+    if (prec == PPL_PREC_BF16X3)
+        k_split_panels<PPL_PREC_BF16X3><<<grid_for(total, 256), 256, 0, st>>>(s, rows, prow, cols, kdiv, kmod, npan,
+                                                                              batch, dst, plane_elems);
+    else if (prec == PPL_PREC_TF32X3)
+        k_split_panels<PPL_PREC_TF32X3><<<grid_for(total, 256), 256, 0, st>>>(s, rows, prow, cols, kdiv, kmod, npan,
+                                                                              batch, dst, plane_elems);
+    else
+        k_split_panels<PPL_PREC_TF32><<<grid_for(total, 256), 256, 0, st>>>(s, rows, prow, cols, kdiv, kmod, npan,
+                                                                            batch, dst, plane_elems);
+}
+
+void transpose_panels(int prec, const void* src, void* dst, long long plane_elems, int n, long long bstride,
+                      int batch, cudaStream_t s) {
+    if (n <= 0 || batch <= 0) return;
+    if (prec == PPL_PREC_BF16X3) {
+        const int t = (n + 63) / 64;
+        k_transpose_panels<unsigned short, 2, 64><<<dim3(t, t, batch), 256, 0, s>>>(
+            (const unsigned short*)src, (unsigned short*)dst, plane_elems, n, bstride);
+    } else {
+        const int t = (n + 31) / 32;
+        if (prec == PPL_PREC_TF32X3)
+            k_transpose_panels<float, 2, 32><<<dim3(t, t, batch), 256, 0, s>>>((const float*)src, (float*)dst,
+                                                                               plane_elems, n, bstride);
+        else
+            k_transpose_panels<float, 1, 32><<<dim3(t, t, batch), 256, 0, s>>>((const float*)src, (float*)dst,
+                                                                               plane_elems, n, bstride);
+    }
 }
 
 void zero_bytes(void* p, size_t n, cudaStream_t s) {

@@ -55,7 +55,9 @@ def test_workspace_grows_with_rank_and_precision_layout(lib):
     b16 = binding.ppl_cpd_workspace_size(5, 24, 72, 48, binding.make_opts("bf16x3"))
     t32 = binding.ppl_cpd_workspace_size(5, 24, 72, 48, binding.make_opts("tf32"))
     big = binding.ppl_cpd_workspace_size(5, 24, 72, 96, binding.make_opts("bf16x3"))
-    assert b16 == t32 and big > b16 and f64 > 0
+    # both 4-byte operand elements; bf16 K panels are 64 elements wide against 32, so
+    # the bf16 layout pads at least as much
+    assert b16 >= t32 and big > b16 and f64 > 0
 
 
 def test_workspace_follows_the_planner_options(lib):
@@ -69,11 +71,11 @@ def test_workspace_follows_the_planner_options(lib):
     assert sizes[0] < sizes[1] < sizes[2]
     big = (20, 200, 600, 3000)
     assert ws(*big, binding.make_opts("tf32x3", r_chunk=1024)) == ws(*big, binding.make_opts("tf32x3", r_chunk=4096))
-    # automatic chunk: all of R while one [rc][X][v] operand buffer stays within 2 GiB ...
+    # automatic chunk: all of R while one [rc][X][v] operand buffer stays within 8 GiB ...
     assert t3 == ws(*shape, binding.make_opts("tf32x3", r_chunk=800))
-    # ... and equal chunks under that budget otherwise (X v 8 bytes = 8.64 MB per column: 10 x 240)
+    # ... and equal chunks under that budget otherwise (X v 8 bytes = 8.64 MB per column: 3 x 800)
     cfg4 = (60, 600, 1800, 2400)
-    assert ws(*cfg4, binding.make_opts("tf32x3")) == ws(*cfg4, binding.make_opts("tf32x3", r_chunk=240))
+    assert ws(*cfg4, binding.make_opts("tf32x3")) == ws(*cfg4, binding.make_opts("tf32x3", r_chunk=800))
     # the dressed D-bar takes room; accumulator restarts take none
     assert ws(*shape, binding.make_opts("tf32x3", dressed=True)) > t3
     assert ws(*shape, binding.make_opts("tf32x3", acc_chunk=2, acc_steps=1)) == t3
