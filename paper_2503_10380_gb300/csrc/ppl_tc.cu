@@ -42,6 +42,14 @@ constexpr int KROW_BYTES = 128;       // one swizzle row: 64 bf16 or 32 fp32
 constexpr int SMEM_BUDGET = 200 * 1024;      // operand stages
 constexpr int SMEM_ATTR = 220 * 1024;        // dynamic smem opt-in (stages + alignment + barriers)
 constexpr unsigned long long WAIT_NS = 500ull * 1000ull * 1000ull;   // 0.5 s per wait
+// Epilogue warps: two per TMEM lane quarter (a warp reads the 32 lanes of its
+// quarter, warp % 4), each draining every other 32-column slice of the tile and,
+// when the accumulator is restarted, holding NSL x 32 running sums.  (Four per
+// quarter measured slower: the drain is not bound by TMEM load latency.)
+constexpr int NEPI = 8;
+constexpr int NTHREADS = 32 * (2 + NEPI);
+constexpr int CSTRIDE = 32 * (NEPI / 4);      // columns between one warp's slices
+constexpr int NSL = 256 / CSTRIDE;            // slices per warp of a 256-column tile
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -184,6 +192,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "memory");
 }
 
+// two FP32 values in one 64-bit register pair, added with one packed
+// round-to-nearest instruction (the same rounding as two scalar adds)
+__device__ __forceinline__ unsigned long long pack2(uint32_t a, uint32_t b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void unpack2(unsigned long long x, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+
 __device__ __forceinline__ float round_tf32(float x) {
     uint32_t y;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
@@ -260,7 +284,7 @@ __device__ __forceinline__ void emit32(const KParams& p, long long mo, int n0, i
 }
 
 template <int PREC, bool DRAIN>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
     constexpr bool SPLIT = (Prec<PREC>::PLANES == 2);
@@ -268,7 +292,6 @@ __global__ void __launch_bounds__(320, 1)
     constexpr int KSTEP = Prec<PREC>::KSTEP;
     constexpr int ASTEP_BYTES = 32;           // one MMA's K slice of a 128-byte row
 
-    constexpr int NEPI = 8;                   // epilogue warps: two per TMEM lane quarter
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn;
     const int tiles_mn = ntm * ntn;
@@ -483,9 +506,9 @@ __global__ void __launch_bounds__(320, 1)
     } else {
         // epilogue: warps 2..9; warp w reads TMEM lanes 32*(w%4) .. +31 and every
         // other 32-column chunk of the accumulator
-        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int q = warp & 3, cg = (warp - 2) >> 2;
         int li = 0;
-        float racc[DRAIN ? 4 : 1][32];   // running sums of the chunks (DRAIN only)
+        unsigned long long racc[DRAIN ? NSL : 1][16];   // running sums of the chunks, packed in pairs (DRAIN only)
         bool ok = true;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const int z = t / tiles_mn, rem = t % tiles_mn;
@@ -509,6 +532,12 @@ __global__ void __launch_bounds__(320, 1)
                 mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(q1 / PW) * p.q1p +
                      (long long)(q1 % PW) * p.q1s + (long long)(q0 / PW) * p.q0p + (long long)(q0 % PW) * p.q0s;
             }
+            if constexpr (DRAIN) {
+#pragma unroll
+                for (int sl = 0; sl < NSL; ++sl)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) racc[sl][j] = 0ull;   // +0.0f, +0.0f
+            }
             for (int c = 0; c < nch; ++c, ++li) {
                 const int buf = li & 1;
                 if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
@@ -526,14 +555,13 @@ __global__ void __launch_bounds__(320, 1)
                 const bool last = (c == nch - 1);
                 if constexpr (DRAIN) {
 #pragma unroll
-                    for (int sl = 0; sl < 4; ++sl) {
-                        const int c0 = half * 32 + sl * 64;
+                    for (int sl = 0; sl < NSL; ++sl) {
+                        const int c0 = cg * 32 + sl * CSTRIDE;
                         if (c0 < p.bn) {
                             uint32_t v[32];
                             tmem_ld32(tb + (uint32_t)c0, v);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                racc[sl][j] = (c == 0 ? 0.0f : racc[sl][j]) + __uint_as_float(v[j]);
+                            for (int j = 0; j < 16; ++j) racc[sl][j] = add2(racc[sl][j], pack2(v[2 * j], v[2 * j + 1]));
                         }
                     }
                     if (last) {
@@ -544,15 +572,20 @@ __global__ void __launch_bounds__(320, 1)
                         if (lane == 0)
                             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
 #pragma unroll
-                        for (int sl = 0; sl < 4; ++sl) {
-                            const int c0 = half * 32 + sl * 64;
+                        for (int sl = 0; sl < NSL; ++sl) {
+                            const int c0 = cg * 32 + sl * CSTRIDE;
                             const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
-                            if (c0 < p.bn && mrow && nvalid > 0) emit32<PREC>(p, mo, n0 + c0, nvalid, racc[sl]);
+                            if (c0 < p.bn && mrow && nvalid > 0) {
+                                float x[32];
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) unpack2(racc[sl][j], x[2 * j], x[2 * j + 1]);
+                                emit32<PREC>(p, mo, n0 + c0, nvalid, x);
+                            }
                         }
                         continue;
                     }
                 } else {
-                    for (int c0 = half * 32; c0 < p.bn; c0 += 64) {
+                    for (int c0 = cg * 32; c0 < p.bn; c0 += CSTRIDE) {
                         uint32_t v[32];
                         tmem_ld32(tb + (uint32_t)c0, v);
                         const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));   // this tile's columns only
@@ -804,9 +837,9 @@ template <int PREC>
 void launch_tc(bool drain, int grid, size_t smem, cudaStream_t s, const CUtensorMap& a, const CUtensorMap& al,
                const CUtensorMap& b, const CUtensorMap& bl, const KParams& p) {
     if (drain)
-        k_tc_gemm<PREC, true><<<grid, 320, smem, s>>>(a, al, b, bl, p);
+        k_tc_gemm<PREC, true><<<grid, NTHREADS, smem, s>>>(a, al, b, bl, p);
     else
-        k_tc_gemm<PREC, false><<<grid, 320, smem, s>>>(a, al, b, bl, p);
+        k_tc_gemm<PREC, false><<<grid, NTHREADS, smem, s>>>(a, al, b, bl, p);
 }
 
 }  // namespace

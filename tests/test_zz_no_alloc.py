@@ -48,7 +48,11 @@ def test_static_energy_matches_workspace_energy_twice(shape):
 
 def test_static_energy_rejects_sizes_beyond_its_array():
     o, R = 1000, 1000      # 2 * o * R * 8 bytes exceed the array; refused before any device work
+    # real device buffers rather than made-up addresses; the call must refuse the
+    # sizes before it reads them
+    B = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fac = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(binding.PplError) as e:
-        binding.ppl_cp_energy_static(o, 10, 10, R, 256, 256, None)
+        binding.ppl_cp_energy_static(o, 10, 10, R, B.data_ptr(), fac.data_ptr(), None)
     assert e.value.code == binding.PPL_EINVAL
     assert "static scratch limit" in str(e.value)
