@@ -65,7 +65,7 @@ typedef struct {
     int r_chunk;     /* columns of r per pass of the chain (workspace grows with it), at most
                         1024; 0 = automatic: equal chunks of at most 256 columns in FP64,
                         on the tensor cores as wide as keeps one [rc][X][v] operand
-                        buffer within 2 GiB                                              */
+                        buffer within 8 GiB                                              */
     int use_graph;   /* 1: capture one sweep in a CUDA graph on first use and replay it  */
     int want_eta;    /* 1: also compute eta, Eqs. (N3_stopping)/(new_conv), each sweep    */
     int profile;     /* 1: record CUDA events between the phases of every sweep           */
@@ -78,7 +78,12 @@ typedef struct {
                         tf32 columns) inside each K block instead: less round-toward-
                         zero bias, more round-to-nearest additions, slower; 0 or -1 =
                         off (the default)                                                */
-    int reserved[8];
+    int wait_limit_us; /* > 0: every bounded device wait of this handle's kernels (grid
+                        barriers of the solve, tensor-core pipeline barriers) gives up
+                        after this many microseconds; 0 = 1 s for the solve, 0.5 s for
+                        the pipeline.  On expiry the kernel records the error, drains
+                        what it issued and returns; the call reports PPL_ETIMEOUT.     */
+    int reserved[7];
 } ppl_cpd_opts;
 
 typedef struct {
@@ -274,6 +279,16 @@ int ppl_cpd_destroy(ppl_cpd* h);
 #define PPL_STATIC_SCRATCH_BYTES (8u << 20)
 int ppl_cp_energy_static(int o, int v, int X, int R, const double* B, const double* factors,
                          double* E_cp, void* stream);
+
+/* Test of the bounded device waits (no counterpart in the paper): arms a one-
+ * shot flag in the handle's device memory so that, in the next mode update,
+ * one block of the cooperative solve does not arrive at its first grid
+ * barrier.  The other blocks' wait then runs out (after opts.wait_limit_us,
+ * or 1 s), every block returns, and the sweep reports PPL_ETIMEOUT and counts
+ * it in ppl_cpd_stats.timeouts.  Nothing faults or hangs and the handle stays
+ * usable; the factors are left mid-update, so reset them
+ * (ppl_cpd_factors_changed) before further sweeps.  Works under graph replay. */
+int ppl_cpd_inject_wait_timeout(ppl_cpd* h);
 
 /* Building-block check of the tensor-core contraction used by the MTTKRP:
  * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the

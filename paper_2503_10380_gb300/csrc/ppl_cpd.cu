@@ -222,6 +222,8 @@ struct ppl_cpd {
     int tc_cap;          // > 0: at most this many CTAs per tensor-core contraction (set inside a batch)
     bool cache_valid;
     long long nsolves;
+    long long ntimeouts;           // bounded device waits that expired (calls that returned PPL_ETIMEOUT)
+    unsigned long long wait_ns;    // opts.wait_limit_us in ns (0: each kernel's default)
     size_t fac_bytes() const { return (size_t)(2 * v + 2 * o + 1) * R * sizeof(double); }
 
     template <class T>
@@ -230,6 +232,7 @@ struct ppl_cpd {
     double* scal() const { return at<double>(L.scal); }
     unsigned long long* nclamp() const { return at<unsigned long long>(L.flags); }
     unsigned int* errflag() const { return reinterpret_cast<unsigned int*>(ws + L.flags + 8); }
+    unsigned int* withhold() const { return reinterpret_cast<unsigned int*>(ws + L.flags + 48); }
     int dim(int m) const { return m < 2 ? v : o; }
     bool tc() const { return opts.precision != PPL_PREC_FP64; }
     // bytes of one operand element over all its planes
@@ -340,6 +343,7 @@ int run_tc(ppl_cpd* h, TcGemm& g, const char* what) {
     g.kchunk = h->kchunk();
     g.ksub = h->ksub();
     g.grid_cap = h->tc_cap;
+    g.wait_ns = h->wait_ns;
     if (g.bn == 0) g.bn = bn_for(g.N);
     const int r = tc_gemm(g, h->errflag(), h->st);
     if (r != 0)
@@ -372,7 +376,7 @@ int solve_mode(ppl_cpd* h, int m) {
                                   h->at<double>(h->L.Zi), h->U[m],
                                   h->lam, h->G(m), reinterpret_cast<unsigned int*>(f + 16),
                                   reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(),
-                                  h->solve_cap, h->st);
+                                  h->solve_cap, h->wait_ns, h->withhold(), h->st);
     if (r != 0)
         return fail(h, PPL_ECUDA, "cooperative solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
                     r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
@@ -866,6 +870,7 @@ int sync_and_check(ppl_cpd* h) {
     cudaMemcpy(&flag, h->errflag(), sizeof flag, cudaMemcpyDeviceToHost);
     if (flag) {
         cudaMemset(h->errflag(), 0, sizeof flag);
+        h->ntimeouts++;
         return fail(h, PPL_ETIMEOUT, "a bounded device wait expired (flags 0x%x)", flag);
     }
     return PPL_OK;
@@ -942,6 +947,8 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     h->tc_cap = 0;
     h->cache_valid = false;
     h->nsolves = 0;
+    h->ntimeouts = 0;
+    h->wait_ns = op.wait_limit_us > 0 ? (unsigned long long)op.wait_limit_us * 1000ull : 0ull;
     if (op.profile) {
         for (int k = 0; k < 9; ++k)
             if (cudaEventCreate(&h->pev[k]) != cudaSuccess) {
@@ -1415,7 +1422,7 @@ int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
     cudaMemcpy(&nc, h->nclamp(), sizeof nc, cudaMemcpyDeviceToHost);
     s->sweeps = h->sweeps;
     s->clamped_pivots = (long long)nc;
-    s->timeouts = 0;
+    s->timeouts = h->ntimeouts;
     s->last_fit = h->have_normR2 ? h->last_hist[0] : nan("");
     s->last_inner = h->last_hist[1];
     s->last_norm2 = h->last_hist[2];
@@ -1427,6 +1434,21 @@ int ppl_cpd_stats_get(ppl_cpd* h, ppl_cpd_stats* s) {
 }
 
 const char* ppl_last_error(const ppl_cpd* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int ppl_cpd_inject_wait_timeout(ppl_cpd* h) {
+    if (!h) return fail(nullptr, PPL_EINVAL, "NULL handle");
+    int e = enter(h);
+    if (e) return e;
+    const unsigned int one = 1u;
+    cudaMemcpyAsync(h->withhold(), &one, sizeof one, cudaMemcpyHostToDevice, h->st);
+    e = check_cuda(h, "inject_wait_timeout");
+    if (!e) {
+        const cudaError_t ce = cudaStreamSynchronize(h->st);
+        if (ce != cudaSuccess) e = fail(h, PPL_ECUDA, "inject_wait_timeout: %s", cudaGetErrorString(ce));
+    }
+    leave(h);
+    return e;
+}
 
 }  // extern "C"
 
@@ -1552,6 +1574,7 @@ int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
                 cudaMemcpy(&flag, h->errflag(), sizeof flag, cudaMemcpyDeviceToHost);
                 if (flag) {
                     cudaMemset(h->errflag(), 0, sizeof flag);
+                    h->ntimeouts++;
                     return fail(nullptr, PPL_ETIMEOUT, "instance %d: a bounded device wait expired (0x%x)", k, flag);
                 }
                 double hist[4];

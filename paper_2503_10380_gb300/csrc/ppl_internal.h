@@ -37,10 +37,12 @@ void hadamard3(const double* G1, const double* G2, const double* G3, int R, doub
 // [ceil(R/32)][32][32] (per diagonal block L[i][j] / L[j][j] below the diagonal and
 // 1 / L[i][i] on it), Z [dim][R], Zi [R][R]; sync (4 words) and maxdiag are reset here.
 // grid_cap > 0 limits the cooperative grid (so that several solves can share the GPU).
+// wait_ns > 0 bounds every barrier wait (default 1 s); *withhold != 0 makes one
+// block skip its first barrier arrival once (the test of the bounded waits).
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
-                    int grid_cap, cudaStream_t s);
+                    int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s);
 // U = Ut / lam (column 2-norms); zero column keeps lam = 0
 void normalise_cols(const double* Ut, int dim, int R, double* U, double* lam, cudaStream_t s);
 // out[0] = sum_{x,r} M[x][r] * Ut[x][r] (Ut = U * lam),  out[1] = lam^T (Ga.Gb.Gi.Gj) lam
@@ -116,6 +118,7 @@ struct TcGemm {
     int ksub;               // > 0: restart it every ksub MMA K steps inside each K block instead
     int nfast;              // 1: tile order N-fastest, so that the N tiles of one A row block run together
     int grid_cap;           // > 0: at most this many persistent CTAs (several contractions can share the GPU)
+    unsigned long long wait_ns;   // > 0: bound of every pipeline barrier wait (default 0.5 s)
     TcOut out;
 };
 int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s);

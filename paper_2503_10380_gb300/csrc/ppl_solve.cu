@@ -46,6 +46,8 @@ struct SolveP {
     unsigned long long* maxdiag;
     unsigned long long* nclamp;
     unsigned int* err;
+    unsigned int* withhold;          // != 0: block 1 skips its first barrier arrival (once)
+    unsigned long long wait_ns;      // bound of every barrier wait
     int R, dim;
 };
 
@@ -76,22 +78,33 @@ __device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int arrived = atom_add_release(&p.sync[0], 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&p.sync[0], 0u);
-            atom_add_release(&p.sync[1], 1u);
-        } else {
+        // the test of the bounded waits: block 1 withholds its first arrival, so
+        // the other blocks' wait runs out; it waits (bounded) for their abort
+        const bool withhold =
+            blockIdx.x == 1 && p.withhold && ld_vol(p.withhold) != 0u && atomicExch(p.withhold, 0u) != 0u;
+        if (withhold) {
             const unsigned long long t0 = gtimer();
-            while (ld_acquire(&p.sync[1]) == gen) {
-                if (ld_vol(&p.sync[2])) {
-                    ok = 0;
-                    break;
-                }
-                if (gtimer() - t0 > BAR_NS) {
-                    atomicExch(&p.sync[2], 1u);
-                    atomicOr(p.err, 16u);
-                    ok = 0;
-                    break;
+            while (!ld_vol(&p.sync[2]) && gtimer() - t0 < 4 * p.wait_ns) {
+            }
+            ok = 0;
+        } else {
+            const unsigned int arrived = atom_add_release(&p.sync[0], 1u) + 1u;
+            if (arrived == gridDim.x) {
+                atomicExch(&p.sync[0], 0u);
+                atom_add_release(&p.sync[1], 1u);
+            } else {
+                const unsigned long long t0 = gtimer();
+                while (ld_acquire(&p.sync[1]) == gen) {
+                    if (ld_vol(&p.sync[2])) {
+                        ok = 0;
+                        break;
+                    }
+                    if (gtimer() - t0 > p.wait_ns) {
+                        atomicExch(&p.sync[2], 1u);
+                        atomicOr(p.err, 16u);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
         }
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                             ok = 0;
                             break;
                         }
-                        if (gtimer() - t0 > BAR_NS) {
+                        if (gtimer() - t0 > p.wait_ns) {
                             atomicExch(&p.sync[2], 1u);
                             atomicOr(p.err, 64u);
                             ok = 0;
@@ -538,7 +551,7 @@ int g_solve_grid = 0;
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
-                    int grid_cap, cudaStream_t s) {
+                    int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s) {
     if (g_solve_grid == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
@@ -563,6 +576,8 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
     p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.Zi = Zi; p.U = U; p.lam = lam;
     p.G = G;
     p.sync = sync; p.maxdiag = maxdiag; p.nclamp = nclamp; p.err = err; p.R = R; p.dim = dim;
+    p.withhold = withhold;
+    p.wait_ns = wait_ns > 0 ? wait_ns : BAR_NS;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);

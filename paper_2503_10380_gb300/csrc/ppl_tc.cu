@@ -66,6 +66,7 @@ struct KParams {
     int ksub;               // > 0: MMA K steps per accumulation chunk, splitting each K block
     int nfast;              // 1: consecutive tiles walk N first (one A tile shared by neighbours)
     int a_panel, b_panel;   // 1: the operand is in the K-panel layout (4-D tensor map)
+    unsigned long long wait_ns;   // bound of every barrier wait
     unsigned int* err;
 };
 
@@ -107,13 +108,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: true when the phase completed, false after WAIT_NS
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// bounded wait: true when the phase completed, false after limit_ns
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (true) {
         if (mbar_try(a, parity)) return true;
-        if (gtimer() - t0 > WAIT_NS) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
 
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int a_b = p.a_b0 + bz * p.a_bstep, b_b = p.b_b0 + bz * p.b_bstep;
                 for (int kbi = 0; kbi < nk; ++kbi, ++it) {
                     const int s = it % S;
-                    if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1))) {
+                    if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1), p.wait_ns)) {
                         atomicOr(p.err, 1u);
                         *vfail = 1;
                         break;
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     // each K block in chunks of ksub MMA K steps, one accumulator each
                     for (int kbi = 0; kbi < nk && ok; ++kbi, ++it) {
                         const int s = it % S;
-                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
+                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
                             atomicOr(p.err, 2u);
                             *vfail = 1;
                             ok = false;
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         for (int kk0 = 0; kk0 < ksteps; kk0 += p.ksub, ++li) {
                             const int kk1 = min(ksteps, kk0 + p.ksub);
                             const int buf = li & 1;
-                            if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
+                            if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
                                 atomicOr(p.err, 8u);
                                 *vfail = 1;
                                 ok = false;
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
                     const int kc1 = min(nk, kc0 + kch);
                     const int buf = li & 1;
-                    if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1))) {
+                    if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
                         atomicOr(p.err, 8u);
                         *vfail = 1;
                         ok = false;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t d = tmem + (uint32_t)buf * acc_cols;
                     for (int kbi = kc0; kbi < kc1; ++kbi, ++it) {
                         const int s = it % S;
-                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1))) {
+                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
                             atomicOr(p.err, 2u);
                             *vfail = 1;
                             ok = false;
@@ -540,7 +541,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             for (int c = 0; c < nch; ++c, ++li) {
                 const int buf = li & 1;
-                if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1))) {
+                if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1), p.wait_ns)) {
                     if (lane == 0) atomicOr(p.err, 4u);
                     *vfail = 1;
                     ok = false;
@@ -606,11 +607,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         // every MMA of this block has completed before TMEM is released
-        if (!mbar_wait(drain_bar, 0)) atomicOr(p.err, 32u);
+        if (!mbar_wait(drain_bar, 0, p.wait_ns)) atomicOr(p.err, 32u);
         if (*vfail) {
             // loads issued but never consumed must land before the block exits
             for (int it = s_consumed; it < s_issued; ++it)
-                if (!mbar_wait(full0 + 8u * (it % S), (uint32_t)((it / S) & 1))) break;
+                if (!mbar_wait(full0 + 8u * (it % S), (uint32_t)((it / S) & 1), p.wait_ns)) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -891,6 +892,7 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     const bool drain = p.ksub > 0 || (g.kchunk > 0 && g.kchunk < p.per_split);
     if (drain && p.bn > 256) return -8;
     p.err = err_flag;
+    p.wait_ns = g.wait_ns > 0 ? g.wait_ns : WAIT_NS;
 
     CUtensorMap mAh, mAl, mBh, mBl;
     const size_t es = half ? 2 : 4;
