@@ -33,10 +33,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "CP-ALS sweeps/s & MTTKRP TFLOP/s at ≤0.1 kcal/mol ΔE vs plain FP64 on GPU"
-O, V, XAUX, RANK, SEED = 20, 200, 600, 800, 0
-SWEEPS_PER_SOLVE = 30          # the configuration's ALS sweep count
+SEED = 0
 KCAL = 627.509474
-WORKLOAD = f"cp-als-ppl single instance o={O} v={V} X={XAUX} R={RANK}, {SWEEPS_PER_SOLVE} sweeps per solve"
+MAIN_CFG = (60, 600, 1800, 2400)   # the largest single-GPU configuration (o, v, X, R)
+CFG1 = (20, 200, 600, 800)
+CFG2 = (40, 400, 1200, 1600)
+O, V, XAUX, RANK = CFG1            # the instance the oracle's flop rate is timed on for estimates
+ACC_SWEEPS_MAIN = 2                # sweeps compared against the FP64 GPU form (about 37 s per FP64 sweep)
+E2E_SWEEPS, E2E_STEPS = 10, 2
+WORKLOAD = (f"cp-als-ppl single instance o={MAIN_CFG[0]} v={MAIN_CFG[1]} X={MAIN_CFG[2]} R={MAIN_CFG[3]}, "
+            f"graph-replayed ALS sweeps")
 
 
 def alg_flops(o, v, X, R):
@@ -155,11 +161,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_from_profile(key: str, src_name: str):
-    """DRAM bytes from the committed ncu summary (profiles/mttkrp_tc_cfg1_traffic.json)
+def traffic_from_profile(key: str, prof_name: str = "mttkrp_tc_cfg4_traffic.json", src_name: str = "ppl_tc.cu"):
+    """DRAM bytes per sweep from a committed ncu summary (profiles/<prof_name>)
     if it was taken on the current source of the kernel; else None."""
     src = os.path.join(ROOT, "paper_2503_10380_gb300", "csrc", src_name)
-    prof = os.path.join(ROOT, "profiles", "mttkrp_tc_cfg1_traffic.json")
+    prof = os.path.join(ROOT, "profiles", prof_name)
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         d = json.load(open(prof))
@@ -172,58 +178,236 @@ def traffic_from_profile(key: str, src_name: str):
 
 def tensor_peak(pk, precision):
     """Algorithmic-flop peak of a tensor-core precision: the dtype's sustained
-    rate divided by the MMAs issued per product (three for the split forms)."""
-    bf16 = pk["bf16_tflops_sustained"]
-    tf32 = bf16 * (1.1 / 2.25)          # nominal dense tf32 / bf16 ratio
-    return {"bf16x3": (bf16 / 3.0, "sustained bf16 / 3 (three bf16 MMAs per product)"),
-            "tf32": (tf32, "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25"),
-            "tf32x3": (tf32 / 3.0, "sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25, / 3 (three tf32 MMAs "
-                                   "per product)")}[precision]
+    rate divided by the MMAs issued per product (three for the split forms).
+    pk: measure_peaks() of this run (TF32); bf16 from MEASURED_PEAKS.json."""
+    bf16 = peaks()[0]["bf16_tflops_sustained"]
+    tf32 = pk["tf32_tflops_sustained"]
+    return {"bf16x3": (bf16 / 3.0, "sustained bf16 (MEASURED_PEAKS.json) / 3 (three bf16 MMAs per product)"),
+            "tf32": (tf32, "sustained TF32 measured in this run"),
+            "tf32x3": (tf32 / 3.0, "sustained TF32 measured in this run / 3 (three tf32 MMAs per product)")}[precision]
 
 
-def fp64_solve_flops(o, v, R):
-    """Algorithmic FP64 flops of the four mode updates of one sweep: per mode
-    2 R^3 / 3 (Cholesky) + 3 dim R^2 (forward and back substitution, Gram)."""
-    return 4 * (2.0 * R ** 3 / 3.0) + 3.0 * R * R * (2 * v + 2 * o)
+def main_config(world):
+    """The workload's identity, the same dict in both arms."""
+    o, v, X, R = MAIN_CFG
+    return {"workload": WORKLOAD, "o": o, "v": v, "X": X, "R": R,
+            "l2": "inputs larger than L2 (tau 10.4 GB, B 5.7 GB)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
-def fp64_peak_tflops(pk):
-    """FP64 FMA peak derived from ncu's sm__sass_thread_inst_executed_op_dfma_pred_on
-    peak_sustained = 2 per clock per SM: 2 FMA x 2 flops x SMs x max SM clock."""
+class _HostInputs:
+    """The oracle's view of one instance: B_vv, tau and the initial factors on the host."""
+
+    def __init__(self, Bvv, tau, factors):
+        self.Bvv, self.tau, self.factors = Bvv, tau, factors
+
+
+def host_inputs(cfg, dev=None):
+    """Seeded inputs of `cfg` for the oracle.  Generated with the torch version of
+    the generator (on the GPU when there is one: setup only, outside every timed
+    region) and copied to host numpy arrays."""
+    import numpy as np
     import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    return 2 * 2 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    from paper_2503_10380_gb300 import inputs
+    o, v, X, R = cfg
+    d = dev if dev is not None else ("cuda" if torch.cuda.is_available() else "cpu")
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=d)
+    Bvv = np.ascontiguousarray(B[:, o:, o:].cpu().numpy())
+    tau_h = tau.cpu().numpy()
+    del B, tau
+    if torch.cuda.is_available():
+        torch.cuda.empty_cache()
+    return _HostInputs(Bvv, tau_h, fac)
+
+
+def oracle_sample(inp, R, budget_s, nsweeps=2):
+    """Oracle sweeps/s of the full rank-R problem from sweeps over its first R_s
+    rank columns: the MTTKRP work of a column does not depend on the others and
+    the R_s-column solves are a negligible part, so the full problem's sweep
+    takes R / R_s times as long.  R_s is sized from a calibration sweep so that
+    the timed sweeps take about budget_s."""
+    t_cal = time_oracle_sweeps(inp, 8, 1)
+    R_s = int(max(8, min(R, budget_s / nsweeps / (t_cal / 8))))
+    t = time_oracle_sweeps(inp, R_s, nsweeps)
+    return (nsweeps * R_s / R) / t, R_s, t
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    from paper_2503_10380_gb300 import inputs
-    inp = inputs.make_inputs(O, V, XAUX, RANK, seed=SEED)
-    # size each step to the budget: a step is one oracle sweep over the first
-    # R_s rank columns (all of them when the budget allows); per-r work is
-    # independent, so sweeps/s of the full problem = (R_s / R) / step time
+    o, v, X, R = MAIN_CFG
+    inp = host_inputs(MAIN_CFG)
+    # each step: one oracle sweep over the first R_s rank columns, R_s sized so
+    # that the whole --steps K --warmup W run stays within about 150 s
     budget = 150.0
-    t_cal = time_oracle_sweeps(inp, 64, 1)
-    per_col = t_cal / 64
-    R_s = int(max(16, min(RANK, (budget / max(args.steps + args.warmup, 1)) / per_col)))
+    t_cal = time_oracle_sweeps(inp, 8, 1)
+    R_s = int(max(8, min(R, (budget / max(args.steps + args.warmup, 1)) / (t_cal / 8))))
     for _ in range(args.warmup):
         time_oracle_sweeps(inp, R_s, 1)
     t = time_oracle_sweeps(inp, R_s, args.steps)
-    value = (args.steps * R_s / RANK) / t
+    value = (args.steps * R_s / R) / t
     cores, how = oracle_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; shapes of the paper's molecules)",
-        "config": {"workload": WORKLOAD, "o": O, "v": V, "X": XAUX, "R": RANK},
+        "config": main_config(1),
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} FP64 oracle sweeps over the first {R_s} of {RANK} rank columns, "
-                                   f"scaled by {R_s}/{RANK}; threads from {how}"},
+                         "sample": f"{args.steps} FP64 oracle sweeps over the first {R_s} of {R} rank columns, "
+                                   f"scaled by {R}/{R_s}; threads from {how}"},
         "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_peaks(dev, stream):
+    """Peaks measured in this run (the roofline denominators): TF32 dense
+    throughput of a square cuBLAS GEMM (8192^3, TF32 allowed), best of 10 (burst)
+    and back to back for about 2 s (sustained); FP64 FMA throughput of the
+    library's own probe kernel.  Measurement only: nothing on the hot path calls
+    cuBLAS."""
+    import torch
+    from paper_2503_10380_gb300 import binding
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    n = 8192
+    a = torch.randn(n, n, device=dev)
+    b = torch.randn(n, n, device=dev)
+    for _ in range(3):
+        c = a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(10):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c = a @ b
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    reps = max(1, int(2000.0 / best))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        c = a @ b
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sust = e0.elapsed_time(e1) / reps
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b, c
+    torch.cuda.empty_cache()
+    fl = 2.0 * n ** 3
+    fp64 = binding.ppl_probe_fp64_peak(stream.cuda_stream)
+    return {"tf32_tflops": fl / (best * 1e-3) / 1e12, "tf32_tflops_sustained": fl / (sust * 1e-3) / 1e12,
+            "fp64_tflops": fp64,
+            "how": "tf32: torch.matmul 8192^3 with TF32 allowed, best of 10 (burst) and back to back for ~2 s "
+                   "(sustained); fp64: ppl_probe_fp64_peak (independent FMA chains on every SM, best of 3)"}
+
+
+def fp64_solve_flops(o, v, R):
+    """Algorithmic FP64 flops of the four mode updates of one sweep, per mode
+    R^3/3 (Cholesky) + 2 dim R^2 (the two triangular solves of M V^-1) + 2 dim R^2
+    (the new factor's Gram matrix)."""
+    return 4 * (R ** 3 / 3.0) + 4.0 * R * R * (2 * v + 2 * o)
+
+
+def _factors_host(cp):
+    return {k: t.cpu().numpy().copy() for k, t in cp.factors().items()}
+
+
+def factor_errors(F, F64):
+    """Relative error of every factor against the FP64 GPU form: normwise, and
+    the worst element relative to the largest entry of its column."""
+    import numpy as np
+    out = {}
+    for m in F64:
+        a, b = np.atleast_2d(F[m]), np.atleast_2d(F64[m])
+        col = np.max(np.abs(a - b), axis=0) / np.maximum(np.max(np.abs(b), axis=0), 1e-300)
+        out[m] = {"norm": float(np.linalg.norm(a - b) / np.linalg.norm(b)), "col_max": float(np.max(col))}
+    return out
+
+
+def _time_sweeps(cp, n, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cp.sweep(n, want_hist=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def _phases(cp, n=3):
+    acc = None
+    for _ in range(n):
+        cp.sweep(1, want_hist=False)
+        ph = cp.phase_ms()
+        acc = ph if acc is None else {k: acc[k] + ph[k] for k in acc}
+    return {k: acc[k] / n for k in acc}
+
+
+MTTKRP_PHASES = ("tau_r", "chain_a", "chain_b", "s_and_p")
+SOLVE_PHASES = ("solve_a", "solve_b", "solve_ij")
+
+
+def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None):
+    """k sweeps from the same start in `precision` and in the plain FP64 GPU form:
+    energy difference (kcal/mol and relative), per-factor errors, and the FP64
+    form's time per sweep (its first sweep captures the graph and is not timed)."""
+    import torch
+    from paper_2503_10380_gb300 import binding
+    mixed = binding.CpAls(B, tau, fac, precision=precision, r_chunk=r_chunk)
+    mixed.sweep(k, want_hist=False)
+    E_mixed, F_mixed = mixed.energy(), _factors_host(mixed)
+    mixed.close()
+    del mixed
+    torch.cuda.empty_cache()
+    f64 = binding.CpAls(B, tau, fac, precision="fp64")
+    f64.sweep(1, want_hist=False)
+    f64_ms = _time_sweeps(f64, k - 1, stream) if k > 1 else None
+    E64, F64 = f64.energy(), _factors_host(f64)
+    f64.close()
+    del f64
+    torch.cuda.empty_cache()
+    d = abs(E_mixed - E64)
+    out = {"sweeps": k, "E_cp_mixed": E_mixed, "E_cp_fp64": E64, "dE_kcal_per_mol": d * KCAL,
+           "dE_rel": d / abs(E64), "meets_0.1_kcal": d * KCAL <= 0.1,
+           "factor_rel_err": factor_errors(F_mixed, F64), "fp64_ms_per_sweep": f64_ms}
+    if E_exact is not None:
+        out["E_exact"] = E_exact
+        out["rank_error_kcal_per_mol"] = abs(E64 - E_exact) * KCAL
+    return out
+
+
+def secondary_config(cfg, precision, k_acc, steps, stream, dev, pk):
+    """A second configuration in the same run: sweep rate, MTTKRP TFLOP/s, and the
+    accuracy of `precision` against the FP64 GPU form after k_acc sweeps."""
+    import torch
+    from paper_2503_10380_gb300 import binding, inputs
+    o, v, X, R = cfg
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=dev)
+    cp = binding.CpAls(B, tau, fac, precision=precision, profile=True)
+    rc = cp.autotune()
+    cp.sweep(3, want_hist=False)
+    ms = _time_sweeps(cp, steps, stream)
+    ph = _phases(cp)
+    cp.close()
+    del cp
+    torch.cuda.empty_cache()
+    mt_ms = sum(ph[q] for q in MTTKRP_PHASES)
+    acc = accuracy_vs_fp64(B, tau, fac, precision, rc, k_acc, stream)
+    del B, tau
+    torch.cuda.empty_cache()
+    tf = alg_flops(o, v, X, R) / (mt_ms / 1e3) / 1e12
+    return {"workload": f"cp-als-ppl single instance o={o} v={v} X={X} R={R}", "o": o, "v": v, "X": X, "R": R,
+            "r_chunk": rc, "sweeps_per_s": 1000.0 / ms, "ms_per_sweep": ms, "mttkrp_tflops": tf,
+            "mttkrp_frac_of_sustained_peak": tf / (pk["tf32_tflops_sustained"] / 3.0), "phase_ms": ph,
+            "accuracy": acc,
+            "speedup_vs_fp64_gpu": (acc["fp64_ms_per_sweep"] / ms) if acc["fp64_ms_per_sweep"] else None}
 
 
 def run_ours(args, world, rank, local):
@@ -238,22 +422,18 @@ def run_ours(args, world, rank, local):
     binding.lib()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    inp = inputs.make_inputs(O, V, XAUX, RANK, seed=SEED)
-    B_h = torch.from_numpy(inp.B).pin_memory()
-    tau_h = torch.from_numpy(inp.tau).pin_memory()
-    B = B_h.to(dev)
-    tau = tau_h.to(dev)
-    stream = torch.cuda.current_stream(dev)
-
-    cp = binding.CpAls(B, tau, inp.factors, precision=args.precision, profile=True, r_chunk=args.r_chunk)
+    pk = measure_peaks(dev, stream)
+    o, v, X, R = MAIN_CFG
+    B, tau, fac = inputs.make_inputs_torch(o, v, X, R, seed=SEED, device=dev)
+    cp = binding.CpAls(B, tau, fac, precision=args.precision, profile=True, r_chunk=args.r_chunk)
     if not args.r_chunk:
         args.r_chunk = cp.autotune()       # the library's own r-chunk autotuner (before the timed region)
-    normR2, E_exact, _ = cp.exact_contract()
     for _ in range(args.warmup):
         cp.sweep(1, want_hist=False)
     torch.cuda.synchronize()
@@ -276,128 +456,87 @@ def run_ours(args, world, rank, local):
     ms = reduce_max(e0.elapsed_time(e1), world, dev)
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1000.0)
-    st = cp.stats()
-    fit_last = st["last_fit"]
+    launches = int(cp.stats()["kernels_per_sweep"])
 
     # ---- phase breakdown (CUDA events recorded by the library on its stream) --
-    nprof = min(args.steps, 5)
-    acc = None
-    for _ in range(nprof):
-        cp.sweep(1, want_hist=False)
-        ph = cp.phase_ms()
-        acc = ph if acc is None else {k: acc[k] + ph[k] for k in acc}
-    phases = {k: acc[k] / nprof for k in acc}
-    mttkrp_ms = phases["tau_r"] + phases["chain_a"] + phases["chain_b"] + phases["s_and_p"]
-    flops = alg_flops(O, V, XAUX, RANK)
+    phases = _phases(cp, min(args.steps, 3))
+    mttkrp_ms = sum(phases[q] for q in MTTKRP_PHASES)
+    solve_ms = sum(phases[q] for q in SOLVE_PHASES)
+    flops = alg_flops(o, v, X, R)
     mttkrp_tflops = flops / (mttkrp_ms / 1000.0) / 1e12
-    cp.close()
-
-    # ---- accuracy and the plain FP64 GPU form from the same start -------------
-    n_cmp = SWEEPS_PER_SOLVE
-    mixed = binding.CpAls(B, tau, inp.factors, precision=args.precision, r_chunk=args.r_chunk)
-    mixed.set_normR2(normR2)
-    M_mixed = mixed.mttkrp("a")              # one MTTKRP from the initial guess, before any sweep
-    fits_mixed = mixed.sweep(n_cmp)
-    E_mixed = mixed.energy()
-    mixed.close()
-    f64 = binding.CpAls(B, tau, inp.factors, precision="fp64")
-    f64.set_normR2(normR2)
-    M_f64 = f64.mttkrp("a")
-
-    def mttkrp_err(M):
-        return float(torch.linalg.norm(M - M_f64) / torch.linalg.norm(M_f64))
-    f64.sweep(1, want_hist=False)          # capture
-    torch.cuda.synchronize()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    fits_f64 = f64.sweep(n_cmp - 1)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    f64_ms = g0.elapsed_time(g1) / (n_cmp - 1)
-    E_f64 = f64.energy()
-    f64.close()
-
-    # ---- the other tensor-core precisions on the same start: speed and accuracy
-    variants = {}
-    for prec in ("bf16x3", "tf32x3"):
-        if prec == args.precision:
-            continue
-        alt = binding.CpAls(B, tau, inp.factors, precision=prec, r_chunk=args.r_chunk)
-        alt.set_normR2(normR2)
-        alt_err = mttkrp_err(alt.mttkrp("a"))
-        alt.sweep(n_cmp, want_hist=False)
-        E_alt = alt.energy()
-        torch.cuda.synchronize()
-        g0.record(stream)
-        alt.sweep(50, want_hist=False)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        variants[prec] = {"sweeps_per_s": 50 * 1000.0 / g0.elapsed_time(g1), "E_cp": E_alt,
-                          "mttkrp_rel_err": alt_err,
-                          "dE_kcal_per_mol": abs(E_alt - E_f64) * KCAL,
-                          "meets_0.1_kcal": abs(E_alt - E_f64) * KCAL <= 0.1}
-        alt.close()
 
     # ---- end to end through the C ABI with host buffers -----------------------
-    # per solve (one CC-like iteration): tau copied from pinned host memory,
-    # its operand copies rebuilt, SWEEPS_PER_SOLVE sweeps warm-started from the
-    # factors already on the device, then factors and fit history read back.
-    # B stays resident (the DF integrals do not change between CC iterations).
-    e2e = binding.CpAls(B, tau, inp.factors, precision=args.precision, r_chunk=args.r_chunk)
-    e2e.set_normR2(normR2)
-    fac_out = torch.empty(e2e.fac.numel(), dtype=torch.float64).pin_memory()
-    tau_dev = e2e.tau
+    # one CC-like step: tau copied from pinned host memory, its operand copies
+    # rebuilt, E2E_SWEEPS sweeps warm-started from the factors on the device,
+    # then the factors and the fit history read back.  B stays resident (the DF
+    # integrals do not change between CC iterations).
+    tau_h = torch.empty(tau.shape, dtype=tau.dtype, pin_memory=True)
+    tau_h.copy_(tau)
+    fac_out = torch.empty(cp.fac.numel(), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        tau_dev.copy_(tau_h, non_blocking=True)
-        binding.ppl_cpd_set_tau(e2e.h, tau_dev.data_ptr())
-        hist = e2e.sweep(SWEEPS_PER_SOLVE, want_hist=True)
-        fac_out.copy_(e2e.fac, non_blocking=True)
+        cp.tau.copy_(tau_h, non_blocking=True)
+        binding.ppl_cpd_set_tau(cp.h, cp.tau.data_ptr())
+        hist = cp.sweep(E2E_SWEEPS, want_hist=True)
+        fac_out.copy_(cp.fac, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
         return hist
 
     e2e_step()
-    n_e2e = 3
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
+    for _ in range(E2E_STEPS):
         e2e_step()
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
-    e2e.close()
-    e2e_value = world * n_e2e * SWEEPS_PER_SOLVE / t_e2e
+    e2e_value = world * E2E_STEPS * E2E_SWEEPS / t_e2e
     h2d = tau_h.numel() * 8
-    d2h = fac_out.numel() * 8 + SWEEPS_PER_SOLVE * 8
+    d2h = fac_out.numel() * 8 + E2E_SWEEPS * 8
+    del tau_h
+    # ||R||^2 and E_exact once, from the tensor-core exact contraction
+    t0 = time.perf_counter()
+    _, E_exact, _ = cp.exact_contract(mixed=True)
+    t_exact = time.perf_counter() - t0
+    cp.close()
+    del cp
+    torch.cuda.empty_cache()
+
+    # ---- accuracy against the plain FP64 GPU form from the same start ---------
+    acc = accuracy_vs_fp64(B, tau, fac, args.precision, args.r_chunk, ACC_SWEEPS_MAIN, stream, E_exact)
+    del B, tau
+    torch.cuda.empty_cache()
+
+    # ---- the other single-instance configurations, in the same run ------------
+    secondary = {}
+    if not args.no_secondary:
+        secondary["o=20 v=200 X=600 R=800"] = secondary_config(CFG1, args.precision, 30, 20, stream, dev, pk)
+        secondary["o=40 v=400 X=1200 R=1600"] = secondary_config(CFG2, args.precision, 5, 10, stream, dev, pk)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) -----------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_or = 2
-        t_or = time_oracle_sweeps(inp, RANK, n_or)
+        hin = host_inputs(MAIN_CFG, dev)
+        val, R_s, t_or = oracle_sample(hin, R, 20.0)
+        del hin
         cores, how = oracle_cores()
-        cpu = {"value": n_or / t_or, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n_or} full FP64 oracle sweeps of the same o={O} v={V} X={XAUX} R={RANK} instance; "
-                         f"threads from {how}"}
+        cpu = {"value": val, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+               "sample": f"2 FP64 oracle sweeps of the o={o} v={v} X={X} instance over its first {R_s} of {R} rank "
+                         f"columns ({t_or:.1f} s), scaled by {R}/{R_s}; threads from {how}"}
 
-    pk, pk_kind = peaks()
-    peak, peak_note = tensor_peak(pk, args.precision)
-    # DRAM bytes per sweep of each roofline's kernels (the same per-sweep unit as `achieved`)
-    traffic_mttkrp = traffic_from_profile("mttkrp_bytes_per_sweep", "ppl_tc.cu")
-    traffic_solve = traffic_from_profile("solve_bytes_per_sweep", "ppl_solve.cu")
-    solve_ms = phases["solve_a"] + phases["solve_b"] + phases["solve_ij"]
-    solve_tflops = fp64_solve_flops(O, V, RANK) / (solve_ms / 1000.0) / 1e12
-    fp64_peak = fp64_peak_tflops(pk)
-    roof_solve = {"bound": "alu", "achieved": solve_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                  "frac": solve_tflops / fp64_peak, "traffic": traffic_solve, "ms_per_sweep": solve_ms,
+    peak_tc = pk["tf32_tflops_sustained"] / 3.0
+    solve_tflops = fp64_solve_flops(o, v, R) / (solve_ms / 1000.0) / 1e12
+    roof_solve = {"bound": "alu", "achieved": solve_tflops, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                  "frac": solve_tflops / pk["fp64_tflops"], "traffic": None, "ms_per_sweep": solve_ms,
                   "kernel": "k_solve (FP64 mode updates, cooperative, 4 launches per sweep)",
-                  "peak_source": "derived: 2 DFMA/clk/SM (ncu peak_sustained) x 2 flops x SMs x max SM clock",
-                  "work": "per sweep 4 x 2R^3/3 + 3 R^2 (2v + 2o) FP64 flops"}
-    roof_mttkrp = {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak, "unit": "TFLOP/s",
-                   "frac": mttkrp_tflops / peak, "traffic": traffic_mttkrp, "ms_per_sweep": mttkrp_ms,
+                  "peak_source": "measured in this run: ppl_probe_fp64_peak (FP64 FMA chains on every SM)",
+                  "work": "per sweep 4 (R^3/3 + 4 dim R^2) FP64 flops: Cholesky, two triangular solves, Gram"}
+    roof_mttkrp = {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak_tc, "unit": "TFLOP/s",
+                   "frac": mttkrp_tflops / peak_tc, "traffic": traffic_from_profile("mttkrp_bytes_per_sweep"),
+                   "ms_per_sweep": mttkrp_ms,
                    "kernel": "k_tc_gemm and its helpers (all MTTKRP contractions of one sweep)",
-                   "peak_source": f"{pk_kind}: {peak_note}",
+                   "peak_source": "measured in this run: sustained TF32 cuBLAS GEMM / 3 (three tf32 MMAs per "
+                                  "product); burst TF32 / 3 = %.1f TFLOP/s" % (pk["tf32_tflops"] / 3.0),
                    "work": "per sweep 4 o^2 v^2 R + 16 X v^2 R algorithmic flops"}
     dominant = roof_mttkrp if mttkrp_ms >= solve_ms else roof_solve
     line = {
@@ -405,34 +544,28 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision,
         "data": "synthetic (seeded; shapes of the paper's molecules)",
-        "config": {"workload": WORKLOAD, "o": O, "v": V, "X": XAUX, "R": RANK,
-                   "precision": args.precision, "r_chunk": args.r_chunk,
-                   "l2": "inputs larger than L2 (tau, B operand planes ~0.5 GB)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": main_config(world),
+        "precision": args.precision, "r_chunk": args.r_chunk,
         "mttkrp_tflops": mttkrp_tflops,
         "phase_ms": phases,
         "roofline": dominant,
         "roofline_mttkrp": roof_mttkrp,
         "roofline_solve": roof_solve,
-        "precision_variants": variants,
-        "fp64_gpu": {"ms_per_sweep": f64_ms, "sweeps_per_s": 1000.0 / f64_ms,
-                     "speedup_mixed_vs_fp64": value / world / (1000.0 / f64_ms)},
-        "accuracy": {"sweeps": n_cmp, "E_cp_mixed": E_mixed, "E_cp_fp64": E_f64,
-                     "dE_kcal_per_mol": abs(E_mixed - E_f64) * KCAL,
-                     "dE_rel": abs(E_mixed - E_f64) / abs(E_f64),
-                     "meets_0.1_kcal": abs(E_mixed - E_f64) * KCAL <= 0.1, "E_exact": E_exact,
-                     "mttkrp_rel_err": mttkrp_err(M_mixed),
-                     "rank_error_kcal_per_mol": abs(E_f64 - E_exact) * KCAL,
-                     "fit_mixed": fits_mixed[-1], "fit_fp64": fits_f64[-1]},
+        "peaks_measured": pk,
+        "fp64_gpu": {"ms_per_sweep": acc["fp64_ms_per_sweep"],
+                     "speedup_mixed_vs_fp64": (acc["fp64_ms_per_sweep"] / ms_per_step)
+                     if acc["fp64_ms_per_sweep"] else None},
+        "accuracy": acc,
+        "exact_contract_s": t_exact,
         "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
-                "step": f"one warm-started solve of {SWEEPS_PER_SOLVE} sweeps: tau H2D, operand rebuild, sweeps, "
-                        f"factors + fit history D2H"},
-        "gpu_launches": int(st["kernels_per_sweep"]) * args.steps,
+                "step": f"one warm-started CC-like step: tau H2D from pinned memory, operand rebuild, {E2E_SWEEPS} "
+                        f"sweeps, factors + fit history D2H"},
+        "secondary": secondary,
+        "gpu_launches": launches * args.steps,
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "clock_samples": ck["samples"],
         "cpu_baseline": cpu,
-        "fit_after_timed": fit_last,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -513,7 +646,8 @@ def run_batch(args, world, rank, local):
         cpu = {"value": (fl_or / flops) / t_or, "unit": "batch sweeps/s", "cores": cores, "kind": "oracle",
                "sample": f"one FP64 oracle sweep of each of the first {k} instances, scaled by flops to all 64; "
                          f"threads from {how}"}
-    pk, pk_kind = peaks()
+    pk = measure_peaks(dev, torch.cuda.current_stream(dev))
+    pk_kind = "measured in this run"
     peak, _ = tensor_peak(pk, args.precision)
     tflops = flops / (ms / args.steps / 1000.0) / 1e12
     value = world * args.steps / (ms / 1000.0)
@@ -543,19 +677,8 @@ PREC_CFG, PREC_SWEEPS = (40, 400, 1200, 1600), 20
 SEQ_CFG, SEQ_STEPS, SEQ_MAX_SWEEPS, SEQ_EPS = (60, 600, 1800, 2400), 15, 50, 1e-6
 
 
-def _factors_host(cp):
-    return {k: t.cpu().numpy().copy() for k, t in cp.factors().items()}
-
-
 def _timed_sweeps(cp, n, stream):
-    import torch
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    cp.sweep(n, want_hist=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / n
+    return _time_sweeps(cp, n, stream)
 
 
 def run_precision(args, world, rank, local):
@@ -621,7 +744,8 @@ def run_precision(args, world, rank, local):
             "kernels_per_sweep": launches, "r_chunk": rc_chosen,
         }
     ms = reduce_max(variants["tf32x3"]["ms_per_sweep"], world, dev)
-    pk, pk_kind = peaks()
+    pk = measure_peaks(dev, torch.cuda.current_stream(dev))
+    pk_kind = "measured in this run"
     peak, peak_note = tensor_peak(pk, "tf32x3")
     tf = variants["tf32x3"]["mttkrp_tflops"]
     line = {
@@ -709,7 +833,8 @@ def run_sequence(args, world, rank, local):
     f64_ms = _timed_sweeps(f64, 1, stream)
     f64.close()
     t_solve = reduce_max(t_solve, world, dev)
-    pk, pk_kind = peaks()
+    pk = measure_peaks(dev, torch.cuda.current_stream(dev))
+    pk_kind = "measured in this run"
     peak, _ = tensor_peak(pk, args.precision)
     tf = alg_flops(o, v, X, R) / (mt_ms / 1000.0) / 1e12
     line = {
@@ -738,13 +863,14 @@ def run_sequence(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16x3", "tf32", "tf32x3"], default=None,
                     help="tensor-core precision of the MTTKRP (default: tf32x3, the split that meets the "
                          "0.1 kcal/mol bar; bf16x3 for --workload batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the o=20 and o=40 configurations of the line")
     ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
     ap.add_argument("--workload", choices=["single", "batch", "precision", "sequence"], default="single",
                     help="single: o=20 v=200 X=600 R=800 (default); batch: 64 uneven instances; "

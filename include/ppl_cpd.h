@@ -83,7 +83,9 @@ typedef struct {
                         after this many microseconds; 0 = 1 s for the solve, 0.5 s for
                         the pipeline.  On expiry the kernel records the error, drains
                         what it issued and returns; the call reports PPL_ETIMEOUT.     */
-    int reserved[7];
+    int acc_steps_p; /* as acc_steps, for the contractions of the S-build (W_b, S, P),
+                        whose result M_j sets lam and so the energy; 0 = as acc_steps */
+    int reserved[6];
 } ppl_cpd_opts;
 
 typedef struct {
@@ -289,6 +291,14 @@ int ppl_cp_energy_static(int o, int v, int X, int R, const double* B, const doub
  * usable; the factors are left mid-update, so reset them
  * (ppl_cpd_factors_changed) before further sweeps.  Works under graph replay. */
 int ppl_cpd_inject_wait_timeout(ppl_cpd* h);
+
+/* Measured FP64 FMA throughput of the current device (no counterpart in the
+ * paper; the peak of the FP64 roofline the benchmark reports the solves
+ * against): independent FMA chains on every SM, eight blocks of 256 threads
+ * per SM, best of three launches of about 50 ms timed with CUDA events on
+ * `stream`.  Writes TFLOP/s (2 flops per FMA) to the host double *tflops.
+ * Allocates nothing (its sink is a static device variable). */
+int ppl_probe_fp64_peak(double* tflops, void* stream);
 
 /* Building-block check of the tensor-core contraction used by the MTTKRP:
  * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4
 class ppl_cpd_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
                 ("profile", c_int), ("dressed", c_int), ("acc_chunk", c_int), ("acc_steps", c_int),
-                ("wait_limit_us", c_int), ("reserved", c_int * 7)]
+                ("wait_limit_us", c_int), ("acc_steps_p", c_int), ("reserved", c_int * 6)]
 
 
 class ppl_cpd_stats(ctypes.Structure):
@@ -89,13 +89,15 @@ def lib() -> ctypes.CDLL:
                                        c_void_p]
     L.ppl_cp_energy_static.restype = c_int
     L.ppl_cpd_inject_wait_timeout.argtypes = [H]
+    L.ppl_probe_fp64_peak.argtypes = [POINTER(c_double), c_void_p]
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
                  "ppl_cpd_set_guess_policy", "ppl_cpd_solve", "ppl_cpd_reconstruct", "ppl_cpd_autotune",
                  "ppl_cpd_set_t1", "ppl_exact_contract_mixed",
                  "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy", "ppl_cpd_batch_kernels",
-                 "ppl_tc_gemm_workspace_size", "ppl_tc_gemm", "ppl_cpd_inject_wait_timeout"):
+                 "ppl_tc_gemm_workspace_size", "ppl_tc_gemm", "ppl_cpd_inject_wait_timeout",
+                 "ppl_probe_fp64_peak"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -108,7 +110,7 @@ def _check(rc: int, h=None):
 
 
 def make_opts(precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
-              dressed=False, acc_chunk=0, acc_steps=0, wait_limit_us=0) -> ppl_cpd_opts:
+              dressed=False, acc_chunk=0, acc_steps=0, wait_limit_us=0, acc_steps_p=0) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -120,6 +122,7 @@ def make_opts(precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False, pro
     o.acc_chunk = int(acc_chunk)
     o.acc_steps = int(acc_steps)
     o.wait_limit_us = int(wait_limit_us)
+    o.acc_steps_p = int(acc_steps_p)
     return o
 
 
@@ -278,6 +281,12 @@ def ppl_cpd_inject_wait_timeout(h):
     _check(lib().ppl_cpd_inject_wait_timeout(h), h)
 
 
+def ppl_probe_fp64_peak(stream_ptr=None) -> float:
+    x = c_double()
+    _check(lib().ppl_probe_fp64_peak(ctypes.byref(x), stream_ptr))
+    return x.value
+
+
 def ppl_cpd_destroy(h):
     _check(lib().ppl_cpd_destroy(h))
 
@@ -312,7 +321,8 @@ class CpAls:
     """
 
     def __init__(self, B, tau, factors, precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False,
-                 profile=False, dressed=False, stream=None, acc_chunk=0, acc_steps=0, wait_limit_us=0):
+                 profile=False, dressed=False, stream=None, acc_chunk=0, acc_steps=0, wait_limit_us=0,
+                 acc_steps_p=0):
         import torch
         self.torch = torch
         X, n, _ = B.shape
@@ -328,7 +338,7 @@ class CpAls:
         parts.append(torch.ones(R, dtype=torch.float64))
         self.fac = torch.cat(parts).to(dev)
         self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile, dressed, acc_chunk, acc_steps,
-                              wait_limit_us)
+                              wait_limit_us, acc_steps_p)
         self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)

@@ -3,6 +3,8 @@
 // fit / energy steps that run in FP64 in every precision mode.
 #include "ppl_internal.h"
 
+#include "../../include/ppl_cpd.h"
+
 #include <cmath>
 #include <cstdio>
 
@@ -417,4 +419,66 @@ void extract_vv(const double* B, int o, int v, int X, double* out, cudaStream_t 
 
 void fill_f64(double* p, size_t n, double val, cudaStream_t s) {
     k_fill<<<grid_for((long long)n, 256), 256, 0, s>>>(p, n, val);
+}
+
+// ---- FP64 FMA throughput probe (measurement of the FP64 roofline's peak) ----
+
+namespace {
+
+constexpr int PROBE_CHAINS = 8;       // independent FMA chains per thread (covers the FMA latency)
+constexpr int PROBE_ITERS = 12000;
+
+__device__ double g_probe_sink;
+
+__global__ void k_dfma_probe(double a, double b, int iters) {
+    double x[PROBE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < PROBE_CHAINS; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) s += x[k];
+    if (s == 1234.5678) g_probe_sink = s;   // keeps the chains live; practically never taken
+}
+
+}  // namespace
+
+extern "C" int ppl_probe_fp64_peak(double* tflops, void* stream) {
+    if (!tflops) return PPL_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();
+        return PPL_ECUDA;
+    }
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return PPL_ECUDA;
+    }
+    // a contraction factor below 1 keeps the chains finite and away from denormals
+    const double a = 0.999999, b = 1e-6;
+    k_dfma_probe<<<blocks, threads, 0, s>>>(a, b, PROBE_ITERS);   // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        k_dfma_probe<<<blocks, threads, 0, s>>>(a, b, PROBE_ITERS);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.0f && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return PPL_ECUDA;
+    const double flops = 2.0 * PROBE_CHAINS * (double)PROBE_ITERS * blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return PPL_OK;
 }
