@@ -169,7 +169,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.Tt = take((size_t)R * v * L.ldk * e);            // per r: rows d, K = c
         L.W = take((size_t)rc * X * L.ldk * e);            // per r: rows Q, K = d
         L.Y = take((size_t)rc * X * L.ldk * e);            // rows r, K = (Q, c)
-        L.WTa = take((size_t)R * v * kX * e);              // per r: rows c, K = Q (all R: written by chain b)
+        L.WTa = take((size_t)rc * v * kX * e);             // per r: rows c, K = Q
         L.WTb = take((size_t)rc * v * kX * e);
         L.S = take((size_t)rc * kvv * e);                  // rows r, K = (c, d)
         {
@@ -574,7 +574,10 @@ int t_tc(ppl_cpd* h) {
     g.out = out_map(opb(h, h->L.T), pT, 0, v, plain(q.ke, q.ke), kpan((long long)v * q.ke), plain(bT, q.ke));
     int rc = run_tc(h, g, "T");
     if (rc) return rc;
-    // T transposed per r: Tt[r] rows d, K c
+    // T transposed per r: Tt[r] rows d, K c.  (A second copy written by the T
+    // epilogue itself would be uncoalesced: consecutive rows d of a tile are a
+    // panel row apart in Tt, and each 128-byte line of Tt takes one element
+    // from each of 32 tiles; the transpose goes through shared memory instead.)
     transpose_panels(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, v, bT, R, h->st);
     return PPL_OK;
 }
@@ -603,10 +606,7 @@ int run_tc_partial(ppl_cpd* h, TcGemm& g, double* out, long long ldo, const char
     return PPL_OK;
 }
 
-// mode b with keep_wa: the W step also stores W_a = B U_a (the new U_a) in the
-// S-build's layout (rows c, K = Q, all R columns), so that the S-build after
-// the mode-b solve does not recompute it
-int chain_tc(ppl_cpd* h, int mode, double* Mout, bool keep_wa = false) {
+int chain_tc(ppl_cpd* h, int mode, double* Mout) {
     const int v = h->v, X = h->X, R = h->R, rc = h->L.rc;
     const Pan q = pan_of(h);
     const long long pBn = (long long)X * v * q.ldk;       // Bn / Bp plane
@@ -625,16 +625,6 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout, bool keep_wa = false) {
         g1.B = pmat(opb(h, h->L.UopA), pU, R, v, 1, R, 0);
         g1.M = X * v; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
         g1.out = out_map(opb(h, h->L.W), pW, 0, v, plain(q.ke, q.ke), kpan((long long)X * q.ke), plain(bW, q.ke));
-        if (mode == 1 && keep_wa) {
-            // element (m = Q*v + c, n = r) also to WTa[r0 + r] rows c, K = Q
-            const long long bWT = (long long)v * q.kX;
-            const size_t es = h->opts.precision == PPL_PREC_BF16X3 ? 2 : 4;
-            g1.out.out2 = (char*)opb(h, h->L.WTa) + (size_t)r0 * bWT * es;
-            g1.out.plane2 = (long long)R * bWT;
-            g1.out.q1p2 = (long long)v * q.ke; g1.out.q1s2 = 1;          // q1 = Q: the consumer's K
-            g1.out.q0p2 = q.ke * q.ke; g1.out.q0s2 = q.ke;               // q0 = c: a row
-            g1.out.np2 = q.ke * bWT; g1.out.ns2 = bWT;                   // n = r
-        }
         int e = run_tc(h, g1, "W");
         if (e) return e;
         // Y[r][Q][c] = sum_d T[r][c][d] W[r][Q][d]   (mode b: Tt, contracting c);
@@ -660,46 +650,45 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout, bool keep_wa = false) {
     return PPL_OK;
 }
 
-// have_wa: WTa already holds W_a = B U_a for every r (written by chain b)
-int p_tc_body(ppl_cpd* h, bool have_wa);
-int p_tc(ppl_cpd* h, bool have_wa = false) {
+int p_tc_body(ppl_cpd* h);
+int p_tc(ppl_cpd* h) {
     h->in_p = true;
-    const int e = p_tc_body(h, have_wa);
+    const int e = p_tc_body(h);
     h->in_p = false;
     return e;
 }
-int p_tc_body(ppl_cpd* h, bool have_wa) {
+// W_a = B U_a and W_b = B U_b are both formed here per r-chunk.  (W_a is also
+// the W of the mode-b chain, but in the layout with c contiguous; the S
+// contraction needs Q contiguous, and writing that second layout from the
+// chain's epilogue would be uncoalesced, one 4-byte L2 request per element.)
+int p_tc_body(ppl_cpd* h) {
     const int o = h->o, v = h->v, X = h->X, R = h->R, rc = h->L.rc;
     const Pan q = pan_of(h);
     const long long pBn = (long long)X * v * q.ldk;
     const long long pU = (long long)R * q.ldk;
     const long long bWT = (long long)v * q.kX;            // one r of WT
-    const long long pWT = (long long)rc * bWT;            // WTb: one chunk
-    const long long pWTa = (long long)R * bWT;            // WTa: all R
-    const size_t es = h->opts.precision == PPL_PREC_BF16X3 ? 2 : 4;
+    const long long pWT = (long long)rc * bWT;            // one chunk of WT
     const long long pS = (long long)rc * q.kvv;
     double* P = h->at<double>(h->L.P);
-    if (!have_wa) uop(h, 0, h->L.UopA);
+    uop(h, 0, h->L.UopA);
     uop(h, 1, h->L.UopB);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
-        for (int w = have_wa ? 1 : 0; w < 2; ++w) {
+        for (int w = 0; w < 2; ++w) {
             // WT[r] rows c, K Q: WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; m = c*X + Q, n = r
             TcGemm g1{};
             g1.A = pmat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.BpW), pBn, v * X, v, 1, (long long)v * X, 0);
             g1.B = pmat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, R, 0);
             g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
-            void* dst = w == 0 ? (void*)((char*)opb(h, h->L.WTa) + (size_t)r0 * bWT * es) : opb(h, h->L.WTb);
-            g1.out = out_map(dst, w == 0 ? pWTa : pWT, 0, X, plain(q.ke, q.ke), kpan((long long)v * q.ke),
-                             plain(bWT, q.ke));
+            g1.out = out_map(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, plain(q.ke, q.ke),
+                             kpan((long long)v * q.ke), plain(bWT, q.ke));
             int e = run_tc(h, g1, "WT");
             if (e) return e;
         }
         // S[r][c][d] = sum_Q WTa[r][c][Q] WTb[r][d][Q]; stored rows r, K (c, d): m = d, n = c, batch r
         TcGemm gs{};
         gs.A = pmat(opb(h, h->L.WTb), pWT, v, X, rc, v, bWT);
-        gs.B = pmat(opb(h, h->L.WTa), pWTa, v, X, R, v, bWT);
-        gs.b_b0 = r0;
+        gs.B = pmat(opb(h, h->L.WTa), pWT, v, X, rc, v, bWT);
         gs.a_bstep = 1; gs.b_bstep = 1;
         gs.M = v; gs.N = v; gs.K = X; gs.batch = rcur; gs.ksplit = 1;
         gs.out = out_map(opb(h, h->L.S), pS, q.ke, 0, Ix{0, 0}, kpan((long long)rc * q.ke), plain(q.ldk * rc, q.ke));
@@ -798,7 +787,7 @@ int prepare_operands(ppl_cpd* h, bool tau_only) {
     zero_bytes(opb(h, h->L.Tt), (size_t)h->R * v * q.ldk * eb, h->st);
     zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * q.ldk * eb, h->st);
     zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * q.ldk * eb, h->st);
-    zero_bytes(opb(h, h->L.WTa), (size_t)h->R * v * q.kX * eb, h->st);
+    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * q.kX * eb, h->st);
     zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * q.kX * eb, h->st);
     zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * q.kvv * eb, h->st);
     zero_bytes(opb(h, h->L.Gop), (size_t)v * q.kvv * eb, h->st);
@@ -864,11 +853,11 @@ int sweep_body(ppl_cpd* h) {
         mark(h, 2);
         if ((e = solve_mode(h, 0))) return e;
         mark(h, 3);
-        if ((e = chain_tc(h, 1, M, true))) return e;
+        if ((e = chain_tc(h, 1, M))) return e;
         mark(h, 4);
         if ((e = solve_mode(h, 1))) return e;
         mark(h, 5);
-        if ((e = p_tc(h, true))) return e;
+        if ((e = p_tc(h))) return e;
     } else {
         t_fp64(h);
         mark(h, 1);

@@ -104,9 +104,6 @@ struct TcOut {
     int mdiv;
     long long q1p, q1s, q0p, q0s, np, ns;
     float alpha;
-    // EPI_SPLIT only: a second copy of every element, in another operand layout
-    // (same row split m -> (q1, q0)), for a later contraction; out2 == nullptr: none
-    void* out2; long long plane2, sb2, q1p2, q1s2, q0p2, q0s2, np2, ns2;
 };
 struct TcGemm {
     int prec;               // PPL_PREC_BF16X3 or PPL_PREC_TF32

@@ -62,8 +62,6 @@ struct KParams {
     long long plane, sb, sk, q1p, q1s, q0p, q0s, np, ns;
     int mdiv;
     float alpha;
-    void* out2;             // EPI_SPLIT: second copy in another layout (nullptr: none)
-    long long plane2, sb2, q1p2, q1s2, q0p2, q0s2, np2, ns2;
     int kchunk;             // K blocks per accumulation chunk (drained kernels)
     int ksub;               // > 0: MMA K steps per accumulation chunk, splitting each K block
     int nfast;              // 1: consecutive tiles walk N first (one A tile shared by neighbours)
@@ -225,12 +223,12 @@ struct ColOff {
     int split;
 };
 template <int PREC>
-__device__ __forceinline__ ColOff coloffs(long long np, long long ns, int n0) {
+__device__ __forceinline__ ColOff coloffs(const KParams& p, int n0) {
     constexpr int PW = Prec<PREC>::KE;
     ColOff c;
-    c.base = (long long)(n0 / PW) * np + (long long)(n0 % PW) * ns;
-    c.ns = ns;
-    c.jump = np - (long long)PW * ns;
+    c.base = (long long)(n0 / PW) * p.np + (long long)(n0 % PW) * p.ns;
+    c.ns = p.ns;
+    c.jump = p.np - (long long)PW * p.ns;
     c.split = PW - n0 % PW;
     return c;
 }
@@ -238,51 +236,41 @@ __device__ __forceinline__ long long col_at(const ColOff& c, int j) {
     return c.base + (long long)j * c.ns + (j >= c.split ? c.jump : 0ll);
 }
 
-// 32 consecutive columns of one row as operand planes of the precision
+// the epilogue's store of 32 consecutive columns n0 .. n0 + 31 of one row
 template <int PREC>
-__device__ __forceinline__ void store_split(void* out, long long plane, long long mo, const ColOff& co, int nvalid,
-                                            const float (&x)[32]) {
-    if constexpr (PREC == PPL_PREC_BF16X3) {
-        __nv_bfloat16* o = (__nv_bfloat16*)out + mo;
-        __nv_bfloat16* ol = o + plane;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < nvalid) {
-                const long long c = col_at(co, j);
-                const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
-                o[c] = hi;
-                ol[c] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
-            }
-        }
-    } else if constexpr (PREC == PPL_PREC_TF32X3) {
-        float* o = (float*)out + mo;
-        float* ol = o + plane;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < nvalid) {
-                const long long c = col_at(co, j);
-                const float hi = round_tf32(x[j]);
-                o[c] = hi;
-                ol[c] = round_tf32(x[j] - hi);
-            }
-        }
-    } else {
-        float* o = (float*)out + mo;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < nvalid) o[col_at(co, j)] = round_tf32(x[j]);
-    }
-}
-
-// the epilogue's store of 32 consecutive columns n0 .. n0 + 31 of one row;
-// mo / mo2: the row's offsets in the output and in the second copy
-template <int PREC>
-__device__ __forceinline__ void emit32(const KParams& p, long long mo, long long mo2, int n0, int nvalid,
-                                       const float (&x)[32]) {
-    const ColOff co = coloffs<PREC>(p.np, p.ns, n0);
+__device__ __forceinline__ void emit32(const KParams& p, long long mo, int n0, int nvalid, const float (&x)[32]) {
+    const ColOff co = coloffs<PREC>(p, n0);
     if (p.kind == EPI_SPLIT) {
-        store_split<PREC>(p.out, p.plane, mo, co, nvalid, x);
-        if (p.out2) store_split<PREC>(p.out2, p.plane2, mo2, coloffs<PREC>(p.np2, p.ns2, n0), nvalid, x);
+        if constexpr (PREC == PPL_PREC_BF16X3) {
+            __nv_bfloat16* o = (__nv_bfloat16*)p.out + mo;
+            __nv_bfloat16* ol = o + p.plane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nvalid) {
+                    const long long c = col_at(co, j);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+                    o[c] = hi;
+                    ol[c] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+                }
+            }
+        } else if constexpr (PREC == PPL_PREC_TF32X3) {
+            float* o = (float*)p.out + mo;
+            float* ol = o + p.plane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nvalid) {
+                    const long long c = col_at(co, j);
+                    const float hi = round_tf32(x[j]);
+                    o[c] = hi;
+                    ol[c] = round_tf32(x[j] - hi);
+                }
+            }
+        } else {
+            float* o = (float*)p.out + mo;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nvalid) o[col_at(co, j)] = round_tf32(x[j]);
+        }
     } else if (p.kind == EPI_F32) {
         float* o = (float*)p.out + mo;
 #pragma unroll
@@ -538,15 +526,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             const int m = m0 + q * 32 + lane;
             const bool mrow = (m < p.M);
-            long long mo = 0, mo2 = 0;
+            long long mo = 0;
             if (mrow) {
                 constexpr int PW = Prec<PREC>::KE;
                 const int q1 = m / p.mdiv, q0 = m % p.mdiv;
                 mo = (long long)bz * p.sb + (long long)ks * p.sk + (long long)(q1 / PW) * p.q1p +
                      (long long)(q1 % PW) * p.q1s + (long long)(q0 / PW) * p.q0p + (long long)(q0 % PW) * p.q0s;
-                if (p.out2)
-                    mo2 = (long long)bz * p.sb2 + (long long)(q1 / PW) * p.q1p2 + (long long)(q1 % PW) * p.q1s2 +
-                          (long long)(q0 / PW) * p.q0p2 + (long long)(q0 % PW) * p.q0s2;
             }
             if constexpr (DRAIN) {
 #pragma unroll
@@ -595,7 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 float x[32];
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) unpack2(racc[sl][j], x[2 * j], x[2 * j + 1]);
-                                emit32<PREC>(p, mo, mo2, n0 + c0, nvalid, x);
+                                emit32<PREC>(p, mo, n0 + c0, nvalid, x);
                             }
                         }
                         continue;
@@ -609,7 +594,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             float x[32];
 #pragma unroll
                             for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
-                            emit32<PREC>(p, mo, mo2, n0 + c0, nvalid, x);
+                            emit32<PREC>(p, mo, n0 + c0, nvalid, x);
                         }
                     }
                 }
@@ -896,10 +881,6 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.sb = g.out.sb; p.sk = g.out.sk;
     p.q1p = g.out.q1p; p.q1s = g.out.q1s; p.q0p = g.out.q0p; p.q0s = g.out.q0s; p.np = g.out.np; p.ns = g.out.ns;
     p.mdiv = g.out.mdiv > 0 ? g.out.mdiv : (1 << 30);
-    p.out2 = g.out.kind == EPI_SPLIT ? g.out.out2 : nullptr;
-    p.plane2 = g.out.plane2; p.sb2 = g.out.sb2;
-    p.q1p2 = g.out.q1p2; p.q1s2 = g.out.q1s2; p.q0p2 = g.out.q0p2; p.q0s2 = g.out.q0s2;
-    p.np2 = g.out.np2; p.ns2 = g.out.ns2;
     if (g.out.alpha != 1.0f) return -9;
     p.alpha = 1.0f;
     p.kchunk = g.kchunk;
