@@ -41,8 +41,18 @@ CFG2 = (40, 400, 1200, 1600)
 O, V, XAUX, RANK = CFG1            # the instance the oracle's flop rate is timed on for estimates
 ACC_SWEEPS_MAIN = 2                # sweeps compared against the FP64 GPU form (about 37 s per FP64 sweep)
 E2E_SWEEPS, E2E_STEPS = 10, 2
-WORKLOAD = (f"cp-als-ppl single instance o={MAIN_CFG[0]} v={MAIN_CFG[1]} X={MAIN_CFG[2]} R={MAIN_CFG[3]}, "
-            f"graph-replayed ALS sweeps")
+def _workload(cfg):
+    return f"cp-als-ppl single instance o={cfg[0]} v={cfg[1]} X={cfg[2]} R={cfg[3]}, graph-replayed ALS sweeps"
+
+
+WORKLOAD = _workload(MAIN_CFG)
+
+
+def set_main_cfg(cfg):
+    """Run the single-instance benchmark (and the reference arm) on another size."""
+    global MAIN_CFG, WORKLOAD
+    MAIN_CFG = tuple(cfg)
+    WORKLOAD = _workload(MAIN_CFG)
 
 
 def alg_flops(o, v, X, R):
@@ -190,8 +200,9 @@ def tensor_peak(pk, precision):
 def main_config(world):
     """The workload's identity, the same dict in both arms."""
     o, v, X, R = MAIN_CFG
+    gb = (o * o * v * v + X * (o + v) ** 2) * 8 / 1e9
     return {"workload": WORKLOAD, "o": o, "v": v, "X": X, "R": R,
-            "l2": "inputs larger than L2 (tau 10.4 GB, B 5.7 GB)",
+            "l2": f"inputs larger than L2 (tau and B {gb:.2f} GB)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
@@ -871,12 +882,15 @@ def main():
                          "0.1 kcal/mol bar; bf16x3 for --workload batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the o=20 and o=40 configurations of the line")
+    ap.add_argument("--config", default="", help="o,v,X,R of the single-instance workload (default 60,600,1800,2400)")
     ap.add_argument("--r-chunk", type=int, default=0, help="rank columns per pass of the MTTKRP chain (0 = auto)")
     ap.add_argument("--workload", choices=["single", "batch", "precision", "sequence"], default="single",
                     help="single: o=20 v=200 X=600 R=800 (default); batch: 64 uneven instances; "
                          "precision: o=40 v=400 X=1200 R=1600 in FP64, BF16x3 and TF32; "
                          "sequence: o=60 v=600 X=1800 R=2400, 15 warm-started CC-like steps")
     args = ap.parse_args()
+    if args.config:
+        set_main_cfg(int(x) for x in args.config.split(","))
     if args.precision is None:
         args.precision = "bf16x3" if args.workload == "batch" else "tf32x3"
     if args.warmup < 3:

@@ -42,14 +42,25 @@ constexpr int KROW_BYTES = 128;       // one swizzle row: 64 bf16 or 32 fp32
 constexpr int SMEM_BUDGET = 200 * 1024;      // operand stages
 constexpr int SMEM_ATTR = 220 * 1024;        // dynamic smem opt-in (stages + alignment + barriers)
 constexpr unsigned long long WAIT_NS = 500ull * 1000ull * 1000ull;   // 0.5 s per wait
-// Epilogue warps: two per TMEM lane quarter (a warp reads the 32 lanes of its
-// quarter, warp % 4), each draining every other 32-column slice of the tile and,
-// when the accumulator is restarted, holding NSL x 32 running sums.  (Four per
-// quarter measured slower: the drain is not bound by TMEM load latency.)
-constexpr int NEPI = 8;
-constexpr int NTHREADS = 32 * (2 + NEPI);
-constexpr int CSTRIDE = 32 * (NEPI / 4);      // columns between one warp's slices
-constexpr int NSL = 256 / CSTRIDE;            // slices per warp of a 256-column tile
+// Block layout: one control warpgroup (warp 0 issues TMA, warp 1 issues the
+// MMAs, warp 2 owns the TMEM allocation, warp 3 idles) and two epilogue
+// warpgroups, warps 4..11: two warps per TMEM lane quarter (a warp reads the 32
+// lanes of its quarter, warp % 4), each draining one 128-column half of the tile
+// as two 64-column slices.  With the accumulator restarted every K block an
+// epilogue thread holds 128 running sums and loads 64 columns per TMEM round
+// trip, more registers than a 384-thread block gives every thread, so the
+// control warpgroup hands registers to the epilogue (setmaxnreg): 56 for it and
+// 224 for each epilogue thread, 128*56 + 256*224 = 384*168, exactly the launch's
+// allocation (checked on the host before every launch: a split above the
+// allocation would wait forever).
+constexpr int NCTRL = 4;                      // warps of the control warpgroup
+constexpr int NEPI = 8;                       // epilogue warps
+constexpr int NTHREADS = 32 * (NCTRL + NEPI);
+constexpr int REG_LAUNCH = 168;               // registers per thread at launch (65536 / 384, rounded to 8)
+constexpr int REG_CTRL = 56, REG_EPI = 224;
+static_assert(32 * NCTRL * REG_CTRL + 32 * NEPI * REG_EPI == NTHREADS * REG_LAUNCH, "register split");
+constexpr int SLW = 64;                       // columns per slice
+constexpr int NSL = 2;                        // slices per epilogue warp (a 128-column half)
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -209,6 +220,30 @@ __device__ __forceinline__ void unpack2(unsigned long long x, float& a, float& b
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
 }
 
+// 64 accumulator columns as two 32-column loads (each into 32 consecutive
+// registers, which the allocator finds more easily than one block of 64) and
+// one wait
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+        "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+          "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+          "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+
 __device__ __forceinline__ float round_tf32(float x) {
     uint32_t y;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
@@ -349,167 +384,172 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *slot_ptr;
     volatile int* vfail = &s_fail;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // TMA producer: one ring of S stages shared by all tiles of this block
-            int it = 0;
-            for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
-                const int z = t / tiles_mn, rem = t % tiles_mn;
-                const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
-                const int bz = z / p.ksplit, ks = z % p.ksplit;
-                const int kb0 = ks * p.per_split;
-                const int nk = min(p.per_split, p.nkb_total - kb0);
-                const int a_b = p.a_b0 + bz * p.a_bstep, b_b = p.b_b0 + bz * p.b_bstep;
-                for (int kbi = 0; kbi < nk; ++kbi, ++it) {
-                    const int s = it % S;
-                    if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1), p.wait_ns)) {
-                        atomicOr(p.err, 1u);
-                        *vfail = 1;
-                        break;
-                    }
-                    const uint32_t sa = base + stage_bytes * s;
-                    const uint32_t fb = full0 + 8u * s;
-                    mbar_expect_tx(fb, stage_bytes);
-                    const int kb = kb0 + kbi;
-                    load_op(sa, &mAh, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
-                    load_op(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
-                    if constexpr (SPLIT) {
-                        load_op(sa + a_bytes, &mAl, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
-                        load_op(sa + 2u * a_bytes + b_bytes, &mBl, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
-                    }
-                    s_issued = it + 1;
-                }
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            // MMA issuer
-            uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
-            idesc |= Prec<PREC>::HALF ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
-            int it = 0, li = 0;   // li counts accumulation chunks (one per tile unless DRAIN)
-            bool ok = true;
-            for (int t = blockIdx.x; t < total && ok && !*vfail; t += gridDim.x) {
-                const int z = t / tiles_mn;
-                const int ks = z % p.ksplit;
-                const int kb0 = ks * p.per_split;
-                const int nk = min(p.per_split, p.nkb_total - kb0);
-                const int kch = DRAIN ? p.kchunk : nk;
-                if (DRAIN && p.ksub > 0) {
-                    // each K block in chunks of ksub MMA K steps, one accumulator each
-                    for (int kbi = 0; kbi < nk && ok; ++kbi, ++it) {
+    // the control warpgroup gives registers to the two epilogue warpgroups (each
+    // role's code is dominated by its own register count)
+    if (warp < NCTRL) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_CTRL) : "memory");
+        if (warp == 0) {
+            if (lane == 0) {
+                // TMA producer: one ring of S stages shared by all tiles of this block
+                int it = 0;
+                for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
+                    const int z = t / tiles_mn, rem = t % tiles_mn;
+                    const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
+                    const int bz = z / p.ksplit, ks = z % p.ksplit;
+                    const int kb0 = ks * p.per_split;
+                    const int nk = min(p.per_split, p.nkb_total - kb0);
+                    const int a_b = p.a_b0 + bz * p.a_bstep, b_b = p.b_b0 + bz * p.b_bstep;
+                    for (int kbi = 0; kbi < nk; ++kbi, ++it) {
                         const int s = it % S;
-                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
-                            atomicOr(p.err, 2u);
+                        if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1), p.wait_ns)) {
+                            atomicOr(p.err, 1u);
                             *vfail = 1;
-                            ok = false;
                             break;
                         }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t sa = base + stage_bytes * s;
-                        const uint32_t sah = sa, sal = sa + a_bytes;
-                        const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
-                        const int kc = (kb0 + kbi) * KE;
-                        int ksteps = KE / KSTEP;
-                        if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
-                        const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
-                        const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
-                        for (int kk0 = 0; kk0 < ksteps; kk0 += p.ksub, ++li) {
-                            const int kk1 = min(ksteps, kk0 + p.ksub);
-                            const int buf = li & 1;
-                            if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
-                                atomicOr(p.err, 8u);
+                        const uint32_t fb = full0 + 8u * s;
+                        mbar_expect_tx(fb, stage_bytes);
+                        const int kb = kb0 + kbi;
+                        load_op(sa, &mAh, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                        load_op(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
+                        if constexpr (SPLIT) {
+                            load_op(sa + a_bytes, &mAl, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                            load_op(sa + 2u * a_bytes + b_bytes, &mBl, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
+                        }
+                        s_issued = it + 1;
+                    }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                // MMA issuer
+                uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
+                idesc |= Prec<PREC>::HALF ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+                int it = 0, li = 0;   // li counts accumulation chunks (one per tile unless DRAIN)
+                bool ok = true;
+                for (int t = blockIdx.x; t < total && ok && !*vfail; t += gridDim.x) {
+                    const int z = t / tiles_mn;
+                    const int ks = z % p.ksplit;
+                    const int kb0 = ks * p.per_split;
+                    const int nk = min(p.per_split, p.nkb_total - kb0);
+                    const int kch = DRAIN ? p.kchunk : nk;
+                    if (DRAIN && p.ksub > 0) {
+                        // each K block in chunks of ksub MMA K steps, one accumulator each
+                        for (int kbi = 0; kbi < nk && ok; ++kbi, ++it) {
+                            const int s = it % S;
+                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
+                                atomicOr(p.err, 2u);
                                 *vfail = 1;
                                 ok = false;
                                 break;
                             }
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const uint32_t d = tmem + (uint32_t)buf * acc_cols;
-                            if constexpr (SPLIT) {
-                                for (int kk = kk0; kk < kk1; ++kk) {
-                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                    mma<PREC>(d, dah + off, dbl + off, idesc, kk > kk0 ? 1u : 0u);
-                                    mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                            const uint32_t sa = base + stage_bytes * s;
+                            const uint32_t sah = sa, sal = sa + a_bytes;
+                            const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+                            const int kc = (kb0 + kbi) * KE;
+                            int ksteps = KE / KSTEP;
+                            if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+                            const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+                            const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+                            for (int kk0 = 0; kk0 < ksteps; kk0 += p.ksub, ++li) {
+                                const int kk1 = min(ksteps, kk0 + p.ksub);
+                                const int buf = li & 1;
+                                if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
+                                    atomicOr(p.err, 8u);
+                                    *vfail = 1;
+                                    ok = false;
+                                    break;
                                 }
-                                for (int kk = kk0; kk < kk1; ++kk) {
-                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                    mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                                const uint32_t d = tmem + (uint32_t)buf * acc_cols;
+                                if constexpr (SPLIT) {
+                                    for (int kk = kk0; kk < kk1; ++kk) {
+                                        const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                        mma<PREC>(d, dah + off, dbl + off, idesc, kk > kk0 ? 1u : 0u);
+                                        mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                                    }
+                                    for (int kk = kk0; kk < kk1; ++kk) {
+                                        const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                        mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                                    }
+                                } else {
+                                    for (int kk = kk0; kk < kk1; ++kk) {
+                                        const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                        mma<PREC>(d, dah + off, dbh + off, idesc, kk > kk0 ? 1u : 0u);
+                                    }
                                 }
-                            } else {
-                                for (int kk = kk0; kk < kk1; ++kk) {
-                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                    mma<PREC>(d, dah + off, dbh + off, idesc, kk > kk0 ? 1u : 0u);
-                                }
+                                mma_commit(tfull0 + 8u * buf);
                             }
-                            mma_commit(tfull0 + 8u * buf);
+                            if (!ok) break;
+                            mma_commit(empty0 + 8u * s);
+                            s_consumed = it + 1;
                         }
-                        if (!ok) break;
-                        mma_commit(empty0 + 8u * s);
-                        s_consumed = it + 1;
+                        continue;
                     }
-                    continue;
-                }
-                for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
-                    const int kc1 = min(nk, kc0 + kch);
-                    const int buf = li & 1;
-                    if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
-                        atomicOr(p.err, 8u);
-                        *vfail = 1;
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d = tmem + (uint32_t)buf * acc_cols;
-                    for (int kbi = kc0; kbi < kc1; ++kbi, ++it) {
-                        const int s = it % S;
-                        if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
-                            atomicOr(p.err, 2u);
+                    for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
+                        const int kc1 = min(nk, kc0 + kch);
+                        const int buf = li & 1;
+                        if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
+                            atomicOr(p.err, 8u);
                             *vfail = 1;
                             ok = false;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t sa = base + stage_bytes * s;
-                        const uint32_t sah = sa, sal = sa + a_bytes;
-                        const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
-                        const int kc = (kb0 + kbi) * KE;
-                        int ksteps = KE / KSTEP;
-                        if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
-                        const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
-                        const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
-                        if constexpr (SPLIT) {
-                            // the small cross products first, while the accumulator is small,
-                            // then hi*hi: fewer round-toward-zero additions at full magnitude
-                            for (int kk = 0; kk < ksteps; ++kk) {
-                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                mma<PREC>(d, dah + off, dbl + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
-                                mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                        const uint32_t d = tmem + (uint32_t)buf * acc_cols;
+                        for (int kbi = kc0; kbi < kc1; ++kbi, ++it) {
+                            const int s = it % S;
+                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
+                                atomicOr(p.err, 2u);
+                                *vfail = 1;
+                                ok = false;
+                                break;
                             }
-                            for (int kk = 0; kk < ksteps; ++kk) {
-                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t sa = base + stage_bytes * s;
+                            const uint32_t sah = sa, sal = sa + a_bytes;
+                            const uint32_t sbh = sa + (SPLIT ? 2u : 1u) * a_bytes, sbl = sbh + b_bytes;
+                            const int kc = (kb0 + kbi) * KE;
+                            int ksteps = KE / KSTEP;
+                            if (p.K - kc < KE) ksteps = (p.K - kc + KSTEP - 1) / KSTEP;
+                            const unsigned long long dah = make_desc(sah), dbh = make_desc(sbh);
+                            const unsigned long long dal = make_desc(sal), dbl = make_desc(sbl);
+                            if constexpr (SPLIT) {
+                                // the small cross products first, while the accumulator is small,
+                                // then hi*hi: fewer round-toward-zero additions at full magnitude
+                                for (int kk = 0; kk < ksteps; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbl + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
+                                    mma<PREC>(d, dal + off, dbh + off, idesc, 1u);
+                                }
+                                for (int kk = 0; kk < ksteps; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbh + off, idesc, 1u);
+                                }
+                            } else {
+                                for (int kk = 0; kk < ksteps; ++kk) {
+                                    const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
+                                    mma<PREC>(d, dah + off, dbh + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
+                                }
                             }
-                        } else {
-                            for (int kk = 0; kk < ksteps; ++kk) {
-                                const unsigned long long off = (unsigned long long)((kk * ASTEP_BYTES) >> 4);
-                                mma<PREC>(d, dah + off, dbh + off, idesc, (kbi > kc0 || kk > 0) ? 1u : 0u);
-                            }
+                            mma_commit(empty0 + 8u * s);
+                            s_consumed = it + 1;
                         }
-                        mma_commit(empty0 + 8u * s);
-                        s_consumed = it + 1;
+                        if (!ok) break;
+                        mma_commit(tfull0 + 8u * buf);
                     }
-                    if (!ok) break;
-                    mma_commit(tfull0 + 8u * buf);
                 }
+                mma_commit(drain_bar);   // completes once every MMA issued here has finished
             }
-            mma_commit(drain_bar);   // completes once every MMA issued here has finished
         }
     } else {
-        // epilogue: warps 2..9; warp w reads TMEM lanes 32*(w%4) .. +31 and every
-        // other 32-column chunk of the accumulator
-        const int q = warp & 3, cg = (warp - 2) >> 2;
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPI) : "memory");
+        // epilogue: warps 4..11; warp w reads TMEM lanes 32*(w%4) .. +31 and
+        // columns cg*128 .. cg*128 + 127 of the accumulator
+        const int q = warp & 3, cg = (warp - NCTRL) >> 2;
         int li = 0;
-        unsigned long long racc[DRAIN ? NSL : 1][16];   // running sums of the chunks, packed in pairs (DRAIN only)
+        float racc[DRAIN ? NSL : 1][SLW];   // running sums of the chunks (DRAIN only)
         bool ok = true;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const int z = t / tiles_mn, rem = t % tiles_mn;
@@ -537,7 +577,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int sl = 0; sl < NSL; ++sl)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) racc[sl][j] = 0ull;   // +0.0f, +0.0f
+                    for (int j = 0; j < SLW; ++j) racc[sl][j] = 0.0f;
             }
             for (int c = 0; c < nch; ++c, ++li) {
                 const int buf = li & 1;
@@ -557,44 +597,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if constexpr (DRAIN) {
 #pragma unroll
                     for (int sl = 0; sl < NSL; ++sl) {
-                        const int c0 = cg * 32 + sl * CSTRIDE;
+                        const int c0 = cg * (NSL * SLW) + sl * SLW;
                         if (c0 < p.bn) {
-                            uint32_t v[32];
-                            tmem_ld32(tb + (uint32_t)c0, v);
+                            uint32_t v[SLW];
+                            tmem_ld64(tb + (uint32_t)c0, v);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) racc[sl][j] = add2(racc[sl][j], pack2(v[2 * j], v[2 * j + 1]));
+                            for (int j = 0; j < SLW; ++j) racc[sl][j] += __uint_as_float(v[j]);
                         }
                     }
                     if (last) {
                         // the sums are in registers: give the accumulator back to the
-                        // MMA warp before the (long) stores of the tile
+                        // MMA warp before the (long) stores of the tile.  (Releasing it
+                        // between the second slice's load and its adds measured slower:
+                        // the loads then serialise behind the first slice's adds.)
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         __syncwarp();
                         if (lane == 0)
                             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * buf) : "memory");
 #pragma unroll
                         for (int sl = 0; sl < NSL; ++sl) {
-                            const int c0 = cg * 32 + sl * CSTRIDE;
-                            const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
-                            if (c0 < p.bn && mrow && nvalid > 0) {
-                                float x[32];
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) unpack2(racc[sl][j], x[2 * j], x[2 * j + 1]);
-                                emit32<PREC>(p, mo, n0 + c0, nvalid, x);
+                            for (int hh = 0; hh < SLW / 32; ++hh) {
+                                const int c0 = cg * (NSL * SLW) + sl * SLW + hh * 32;
+                                const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));
+                                if (c0 < p.bn && mrow && nvalid > 0) {
+                                    float x[32];
+#pragma unroll
+                                    for (int j = 0; j < 32; ++j) x[j] = racc[sl][hh * 32 + j];
+                                    emit32<PREC>(p, mo, n0 + c0, nvalid, x);
+                                }
                             }
                         }
                         continue;
                     }
                 } else {
-                    for (int c0 = cg * 32; c0 < p.bn; c0 += CSTRIDE) {
-                        uint32_t v[32];
-                        tmem_ld32(tb + (uint32_t)c0, v);
-                        const int nvalid = min(min(32, p.bn - c0), p.N - (n0 + c0));   // this tile's columns only
-                        if (mrow && nvalid > 0) {
-                            float x[32];
+                    for (int c0 = cg * (NSL * SLW); c0 < min(p.bn, (cg + 1) * NSL * SLW); c0 += SLW) {
+                        uint32_t v[SLW];
+                        tmem_ld64(tb + (uint32_t)c0, v);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
-                            emit32<PREC>(p, mo, n0 + c0, nvalid, x);
+                        for (int hh = 0; hh < SLW / 32; ++hh) {
+                            const int c1 = c0 + hh * 32;
+                            const int nvalid = min(min(32, p.bn - c1), p.N - (n0 + c1));   // this tile's columns only
+                            if (mrow && nvalid > 0) {
+                                float x[32];
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[hh * 32 + j]);
+                                emit32<PREC>(p, mo, n0 + c1, nvalid, x);
+                            }
                         }
                     }
                 }
@@ -826,6 +875,14 @@ int tc_init_driver() {
                 cudaGetLastError();
                 return -2;
             }
+            // the setmaxnreg split assumes exactly REG_LAUNCH registers per thread at
+            // launch; with fewer, the epilogue's increase would wait forever
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) {
+                cudaGetLastError();
+                return -2;
+            }
+            if (fa.numRegs != REG_LAUNCH || fa.maxThreadsPerBlock < NTHREADS) return -12;
         }
         attr_done = true;
     }
@@ -863,7 +920,7 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.M = g.M; p.N = g.N; p.K = g.K;
     p.bn = g.bn > 0 ? g.bn : choose_bn(g.N);
     if (p.bn % 16 || p.bn > 256) return -8;
-    p.acc_cols = 32;
+    p.acc_cols = SLW;      // at least one 64-column slice per accumulator, so no TMEM load leaves its buffer
     while (p.acc_cols < p.bn) p.acc_cols <<= 1;
     p.nkb_total = (g.K + KE - 1) / KE;
     p.ksplit = g.ksplit > 0 ? g.ksplit : 1;
