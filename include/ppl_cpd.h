@@ -300,6 +300,12 @@ int ppl_cpd_inject_wait_timeout(ppl_cpd* h);
  * Allocates nothing (its sink is a static device variable). */
 int ppl_probe_fp64_peak(double* tflops, void* stream);
 
+/* Self-test of the reciprocal the Cholesky uses for its pivots (no counterpart
+ * in the paper): out[i] = the solve kernel's 1/d[i] for n positive normal
+ * doubles d (device arrays), computed with the same device function.  The call
+ * synchronises `stream`.  PPL_EINVAL for NULL arrays or n < 0. */
+int ppl_test_reciprocal(const double* d, double* out, int n, void* stream);
+
 /* Building-block check of the tensor-core contraction used by the MTTKRP:
  * C[M][N] = A[M][K] . B[N][K]^T for FP32 device inputs, computed with the
  * given PPL_PREC_BF16X3, PPL_PREC_TF32 or PPL_PREC_TF32X3 tcgen05 kernel

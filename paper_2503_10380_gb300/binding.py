@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
     L.ppl_cp_energy_static.restype = c_int
     L.ppl_cpd_inject_wait_timeout.argtypes = [H]
     L.ppl_probe_fp64_peak.argtypes = [POINTER(c_double), c_void_p]
+    L.ppl_test_reciprocal.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     for name in ("ppl_cpd_workspace_size", "ppl_cpd_init", "ppl_cpd_mttkrp", "ppl_cpd_sweep",
                  "ppl_cpd_set_normR2", "ppl_cpd_fit", "ppl_cpd_energy", "ppl_exact_contract",
                  "ppl_cpd_set_tau", "ppl_cpd_stats_get", "ppl_cpd_destroy", "ppl_cpd_phase_ms", "ppl_cpd_factors_changed",
@@ -97,7 +98,7 @@ def lib() -> ctypes.CDLL:
                  "ppl_cpd_set_t1", "ppl_exact_contract_mixed",
                  "ppl_cpd_batch_create", "ppl_cpd_batch_sweep", "ppl_cpd_batch_destroy", "ppl_cpd_batch_kernels",
                  "ppl_tc_gemm_workspace_size", "ppl_tc_gemm", "ppl_cpd_inject_wait_timeout",
-                 "ppl_probe_fp64_peak"):
+                 "ppl_probe_fp64_peak", "ppl_test_reciprocal"):
         getattr(L, name).restype = c_int
     _lib = L
     return L

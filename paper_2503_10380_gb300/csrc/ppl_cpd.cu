@@ -404,19 +404,30 @@ void gram(ppl_cpd* h, int m) {
     gemm64(g, h->st);
 }
 
-// solve the normal equations of mode m from M (in L.M), update U[m], lam, G[m]
-int solve_mode(ppl_cpd* h, int m) {
-    const int R = h->R, dim = h->dim(m);
+// the arguments of mode m's update: V from the other three Gram matrices, M from L.M
+SolveArgs solve_args(ppl_cpd* h, int m) {
     int oth[3], k = 0;
     for (int q = 0; q < 4; ++q)
         if (q != m) oth[k++] = q;
     char* f = h->ws + h->L.flags;
-    const int r = solve_mode_coop(h->G(oth[0]), h->G(oth[1]), h->G(oth[2]), h->at<double>(h->L.M), dim, R,
-                                  h->at<double>(h->L.V), h->at<double>(h->L.Linv), h->at<double>(h->L.Z),
-                                  h->at<double>(h->L.Zi), h->U[m],
-                                  h->lam, h->G(m), reinterpret_cast<unsigned int*>(f + 16),
-                                  reinterpret_cast<unsigned long long*>(f + 32), h->nclamp(), h->errflag(),
-                                  h->solve_cap, h->wait_ns, h->withhold(), h->st);
+    SolveArgs a;
+    a.G1 = h->G(oth[0]); a.G2 = h->G(oth[1]); a.G3 = h->G(oth[2]);
+    a.M = h->at<double>(h->L.M);
+    a.dim = h->dim(m); a.R = h->R;
+    a.V = h->at<double>(h->L.V); a.Linv = h->at<double>(h->L.Linv); a.Z = h->at<double>(h->L.Z);
+    a.Zi = h->at<double>(h->L.Zi); a.U = h->U[m]; a.lam = h->lam; a.G = h->G(m);
+    a.sync = reinterpret_cast<unsigned int*>(f + 16);
+    a.maxdiag = reinterpret_cast<unsigned long long*>(f + 32);
+    a.nclamp = h->nclamp(); a.err = h->errflag();
+    a.wait_ns = h->wait_ns; a.withhold = h->withhold();
+    return a;
+}
+
+// solve the normal equations of mode m from M (in L.M), update U[m], lam, G[m]
+int solve_mode(ppl_cpd* h, int m) {
+    const SolveArgs a = solve_args(h, m);
+    const int r = solve_mode_coop(a.G1, a.G2, a.G3, a.M, a.dim, a.R, a.V, a.Linv, a.Z, a.Zi, a.U, a.lam, a.G, a.sync,
+                                  a.maxdiag, a.nclamp, a.err, h->solve_cap, a.wait_ns, a.withhold, h->st);
     if (r != 0)
         return fail(h, PPL_ECUDA, "cooperative solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
                     r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
@@ -833,65 +844,84 @@ void mark(ppl_cpd* h, int k) {
     if (h->opts.profile) cudaEventRecordWithFlags(h->pev[k], h->st, cudaEventRecordExternal);
 }
 
-int sweep_body(ppl_cpd* h) {
-    const int o = h->o, v = h->v, R = h->R;
+// One sweep in five phases; phase q = 0..3 leaves mode q's MTTKRP in L.M and is
+// followed by mode q's solve, phase 4 forms the fit terms (and eta).
+int sweep_phase(ppl_cpd* h, int q) {
+    const int o = h->o, R = h->R;
     double* M = h->at<double>(h->L.M);
-    double* hist = h->at<double>(h->L.hist);
-    if (h->opts.want_eta) {
-        for (int m = 0; m < 4; ++m)
-            cudaMemcpyAsync(h->at<double>(h->L.Uold[m]), h->U[m], (size_t)h->dim(m) * R * sizeof(double),
-                            cudaMemcpyDeviceToDevice, h->st);
-        cudaMemcpyAsync(h->at<double>(h->L.lamold), h->lam, (size_t)R * sizeof(double), cudaMemcpyDeviceToDevice,
-                        h->st);
-    }
-    int e;
-    mark(h, 0);
-    if (h->tc()) {
-        if ((e = t_tc(h))) return e;
-        mark(h, 1);
-        if ((e = chain_tc(h, 0, M))) return e;
-        mark(h, 2);
-        if ((e = solve_mode(h, 0))) return e;
-        mark(h, 3);
-        if ((e = chain_tc(h, 1, M))) return e;
-        mark(h, 4);
-        if ((e = solve_mode(h, 1))) return e;
-        mark(h, 5);
-        if ((e = p_tc(h))) return e;
-    } else {
-        t_fp64(h);
-        mark(h, 1);
-        mttkrp_ab_fp64(h, 0, M);
-        mark(h, 2);
-        if ((e = solve_mode(h, 0))) return e;
-        mark(h, 3);
-        mttkrp_ab_fp64(h, 1, M);
-        mark(h, 4);
-        if ((e = solve_mode(h, 1))) return e;
-        mark(h, 5);
-        p_fp64(h);
-    }
-    mark(h, 6);
     double* P = h->at<double>(h->L.P);
-    occ_mttkrp(P, R, h->U[3], o, R, 0, M, h->st);
-    if ((e = solve_mode(h, 2))) return e;
-    occ_mttkrp(P, R, h->U[2], o, R, 1, M, h->st);
-    if ((e = solve_mode(h, 3))) return e;
-    mark(h, 7);
-    double* sc = h->scal();
-    fit_terms(M, h->U[3], h->lam, o, R, h->G(0), h->G(1), h->G(2), h->G(3), h->at<double>(h->L.partial),
-              sc + SC_TERMS, h->st);
-    finish_fit(sc + SC_TERMS, sc + SC_NORMR2, hist, h->st);
-    if (h->opts.want_eta) {
-        for (int m = 0; m < 4; ++m) cross_gram(h, m);
-        eta_terms(h->at<double>(h->L.Xc[0]), h->at<double>(h->L.Xc[1]), h->at<double>(h->L.Xc[2]),
-                  h->at<double>(h->L.Xc[3]), h->lam, h->at<double>(h->L.lamold), R, h->at<double>(h->L.partial),
-                  sc + SC_CROSS, h->st);
-        finish_eta(sc + SC_CROSS, sc + SC_TERMS + 1, sc + SC_NORM2_PREV, hist, h->st);
-        cudaMemcpyAsync(sc + SC_NORM2_PREV, sc + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    int e = PPL_OK;
+    switch (q) {
+    case 0:
+        if (h->opts.want_eta) {
+            for (int m = 0; m < 4; ++m)
+                cudaMemcpyAsync(h->at<double>(h->L.Uold[m]), h->U[m], (size_t)h->dim(m) * R * sizeof(double),
+                                cudaMemcpyDeviceToDevice, h->st);
+            cudaMemcpyAsync(h->at<double>(h->L.lamold), h->lam, (size_t)R * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->st);
+        }
+        mark(h, 0);
+        if (h->tc()) {
+            if ((e = t_tc(h))) return e;
+            mark(h, 1);
+            if ((e = chain_tc(h, 0, M))) return e;
+        } else {
+            t_fp64(h);
+            mark(h, 1);
+            mttkrp_ab_fp64(h, 0, M);
+        }
+        mark(h, 2);
+        break;
+    case 1:
+        mark(h, 3);
+        if (h->tc()) {
+            if ((e = chain_tc(h, 1, M))) return e;
+        } else {
+            mttkrp_ab_fp64(h, 1, M);
+        }
+        mark(h, 4);
+        break;
+    case 2:
+        mark(h, 5);
+        if (h->tc()) {
+            if ((e = p_tc(h))) return e;
+        } else {
+            p_fp64(h);
+        }
+        mark(h, 6);
+        occ_mttkrp(P, R, h->U[3], o, R, 0, M, h->st);
+        break;
+    case 3:
+        occ_mttkrp(P, R, h->U[2], o, R, 1, M, h->st);
+        break;
+    default: {
+        mark(h, 7);
+        double* sc = h->scal();
+        double* hist = h->at<double>(h->L.hist);
+        fit_terms(M, h->U[3], h->lam, o, R, h->G(0), h->G(1), h->G(2), h->G(3), h->at<double>(h->L.partial),
+                  sc + SC_TERMS, h->st);
+        finish_fit(sc + SC_TERMS, sc + SC_NORMR2, hist, h->st);
+        if (h->opts.want_eta) {
+            for (int m = 0; m < 4; ++m) cross_gram(h, m);
+            eta_terms(h->at<double>(h->L.Xc[0]), h->at<double>(h->L.Xc[1]), h->at<double>(h->L.Xc[2]),
+                      h->at<double>(h->L.Xc[3]), h->lam, h->at<double>(h->L.lamold), R,
+                      h->at<double>(h->L.partial), sc + SC_CROSS, h->st);
+            finish_eta(sc + SC_CROSS, sc + SC_TERMS + 1, sc + SC_NORM2_PREV, hist, h->st);
+            cudaMemcpyAsync(sc + SC_NORM2_PREV, sc + SC_TERMS + 1, sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+        }
+        mark(h, 8);
     }
-    mark(h, 8);
-    (void)v;
+    }
+    return PPL_OK;
+}
+
+int sweep_body(ppl_cpd* h) {
+    int e;
+    for (int q = 0; q < 4; ++q) {
+        if ((e = sweep_phase(h, q))) return e;
+        if ((e = solve_mode(h, q))) return e;
+    }
+    if ((e = sweep_phase(h, 4))) return e;
     return check_cuda(h, "sweep");
 }
 
@@ -1576,21 +1606,43 @@ int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
     if (!b->ready) {
         cudaError_t ce = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
         if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch capture: %s", cudaGetErrorString(ce));
-        cudaEventRecord(b->fork, b->origin);
+        // Phase by phase: every instance's contractions of a phase on the forked
+        // streams, then one cooperative launch that solves that mode for all
+        // instances at once (each on its share of the SMs, with its own barriers).
         int err = PPL_OK;
-        for (size_t i = 0; i < b->streams.size(); ++i) cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-        for (int k = 0; k < n && !err; ++k) {
-            ppl_cpd* h = b->hs[k];
-            cudaStream_t keep = h->st;
-            h->st = b->streams[k % b->streams.size()];
-            err = sweep_body(h);
-            h->st = keep;
-            if (err) g_err = h->err;
+        auto fork = [&]() {
+            cudaEventRecord(b->fork, b->origin);
+            for (size_t i = 0; i < b->streams.size(); ++i) cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        };
+        auto join = [&]() {
+            for (size_t i = 0; i < b->streams.size(); ++i) {
+                cudaEventRecord(b->joins[i], b->streams[i]);
+                cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+            }
+        };
+        std::vector<SolveArgs> args(n);
+        fork();
+        for (int q = 0; q < 5 && !err; ++q) {
+            for (int k = 0; k < n && !err; ++k) {
+                ppl_cpd* h = b->hs[k];
+                cudaStream_t keep = h->st;
+                h->st = b->streams[k % b->streams.size()];
+                err = sweep_phase(h, q);
+                h->st = keep;
+                if (err) g_err = h->err;
+            }
+            if (q == 4 || err) break;
+            join();
+            for (int k = 0; k < n; ++k) args[k] = solve_args(b->hs[k], q);
+            const int r = solve_modes_batched(args.data(), n, b->origin);
+            if (r != 0) {
+                err = fail(nullptr, PPL_ECUDA, "batched solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",
+                           r <= -1000 ? cudaGetErrorString((cudaError_t)(-r - 1000)) : "");
+                break;
+            }
+            fork();
         }
-        for (size_t i = 0; i < b->streams.size(); ++i) {
-            cudaEventRecord(b->joins[i], b->streams[i]);
-            cudaStreamWaitEvent(b->origin, b->joins[i], 0);
-        }
+        join();
         cudaGraph_t gr = nullptr;
         ce = cudaStreamEndCapture(b->origin, &gr);
         if (err) {

@@ -43,6 +43,20 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
                     int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s);
+// The same mode update for several instances in one cooperative launch (at most
+// 64 per launch; more are launched in turn on s): instance k gets its own blocks
+// and barrier words (a[k].sync); the blocks are shared out by FP64 work.
+struct SolveArgs {
+    const double *G1, *G2, *G3, *M;
+    int dim, R;
+    double *V, *Linv, *Z, *Zi, *U, *lam, *G;
+    unsigned int* sync;
+    unsigned long long *maxdiag, *nclamp;
+    unsigned int* err;
+    unsigned long long wait_ns;
+    unsigned int* withhold;
+};
+int solve_modes_batched(const SolveArgs* a, int n, cudaStream_t s);
 // U = Ut / lam (column 2-norms); zero column keeps lam = 0
 void normalise_cols(const double* Ut, int dim, int R, double* U, double* lam, cudaStream_t s);
 // out[0] = sum_{x,r} M[x][r] * Ut[x][r] (Ut = U * lam),  out[1] = lam^T (Ga.Gb.Gi.Gj) lam

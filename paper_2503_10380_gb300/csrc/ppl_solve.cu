@@ -74,14 +74,14 @@ __device__ __forceinline__ unsigned int atom_add_release(unsigned int* p, unsign
 // grid-wide barrier; false when the wait expired or another block aborted.
 // The block's writes are ordered before its arrival by __syncthreads and the
 // release of the arrival; the waiters' acquire loads order what follows.
-__device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
+__device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag, int bid, int G) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         // the test of the bounded waits: block 1 withholds its first arrival, so
         // the other blocks' wait runs out; it waits (bounded) for their abort
         const bool withhold =
-            blockIdx.x == 1 && p.withhold && ld_vol(p.withhold) != 0u && atomicExch(p.withhold, 0u) != 0u;
+            bid == 1 && p.withhold && ld_vol(p.withhold) != 0u && atomicExch(p.withhold, 0u) != 0u;
         if (withhold) {
             const unsigned long long t0 = gtimer();
             while (!ld_vol(&p.sync[2]) && gtimer() - t0 < 4 * p.wait_ns) {
@@ -89,7 +89,7 @@ __device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag) {
             ok = 0;
         } else {
             const unsigned int arrived = atom_add_release(&p.sync[0], 1u) + 1u;
-            if (arrived == gridDim.x) {
+            if (arrived == (unsigned int)G) {
                 atomicExch(&p.sync[0], 0u);
                 atom_add_release(&p.sync[1], 1u);
             } else {
@@ -237,7 +237,9 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
+// One mode update of one instance, run by blocks bid = 0 .. G-1 (of one launch,
+// or of one instance's share of a batched launch); the barriers count G blocks.
+__device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const int G) {
     __shared__ double Ls[NB][NB + 1];
     __shared__ double Li[NB][NB + 1];
     __shared__ double Ta[NB][NB + 1];
@@ -250,8 +252,8 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
 
     const int R = p.R, dim = p.dim;
     const int tid = threadIdx.x;
-    const long long gtid = (long long)blockIdx.x * NT + tid;
-    const long long gthreads = (long long)gridDim.x * NT;
+    const long long gtid = (long long)bid * NT + tid;
+    const long long gthreads = (long long)G * NT;
     if (tid == 0) s_gen = ld_vol(&p.sync[1]);
     for (int i = 0, e = 0; i < NB; ++i)
         for (int c = 0; c <= i; ++c, ++e)
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     }
     for (long long e = gtid; e < (long long)dim * R; e += gthreads) p.Z[e] = p.M[e];
     for (long long e = gtid; e < (long long)R * R; e += gthreads) p.Zi[e] = (e / R == e % R) ? 1.0 : 0.0;
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
         // the first diagonal block straight from the Gram matrices
         for (int e = tid; e < kb0 * kb0; e += NT) {
             const int i = e / kb0, j = e % kb0;
@@ -292,12 +294,11 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         __syncthreads();
         factor_block(p, 0, tol, Ls, Li, rd, tri, Tb);
     }
-    if (!gsync(p, gen, &s_flag)) return;
+    if (!gsync(p, gen, &s_flag, bid, G)) return;
 
     const int nt = (R + NB - 1) / NB;
     const int D = (dim + NB - 1) / NB;
     const int tx = tid % 16, ty = tid / 16;
-    const int G = gridDim.x;
 
     // ---- P1: Cholesky with the forward substitution fused, one block of look-ahead
     for (int k = 0; k < nt; ++k) {
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         // one warp per row solves x L^T = a: with val_q final, x_q = val_q / L_qq
         // and val_t -= val_q (L_tq / L_qq), so each column costs one FMA
         const int ntask = (prow + 7) / 8;
-        for (int task = blockIdx.x; task < ntask; task += G) {
+        for (int task = bid; task < ntask; task += G) {
             const int rr = task * 8 + tid / NB, t = tid % NB;
             double* row = nullptr;
             if (rr < vrows)
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
                 if (t < kb) row[t] = val * Li[t][t];
             }
         }
-        if (!gsync(p, gen, &s_flag)) return;
+        if (!gsync(p, gen, &s_flag, bid, G)) return;
         // trailing update of V (lower tiles) and of Z.  Tile 0 is the next
         // diagonal block: block 0 updates it and factors it while the other
         // blocks take the remaining tiles.
@@ -341,8 +342,8 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         // blocks 1 and 2 then signal block 0, which factors the block once both
         // quarters have landed.  Block 0 takes no other tile.
         const bool split0 = (G >= 3 && k + 1 < nt && ntile > 0);
-        if (split0 && blockIdx.x < 3) {
-            const int q = blockIdx.x;
+        if (split0 && bid < 3) {
+            const int q = bid;
             const int d0 = k0 + kb, nb1 = min(NB, R - d0);
             const int r0 = (q == 0) ? 0 : 16, c0 = (q == 2) ? 16 : 0;
             const double* Pd = p.V + (long long)d0 * R + k0;     // rows of the panel at the next block
@@ -390,11 +391,11 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
         if (G == 1) {
             first = 0;
             stride = 1;
-        } else if (blockIdx.x == 0) {
+        } else if (bid == 0) {
             first = split0 ? ntile : 0;   // tile 0 only, unless split above
             stride = ntile + 1;
         } else {
-            first = blockIdx.x;
+            first = bid;
             stride = G - 1;
         }
         for (int tile = first; tile < ntile; tile += stride) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             __syncthreads();
             if (tile == 0 && k + 1 < nt && !split0) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
         }
-        if (!gsync(p, gen, &s_flag)) return;
+        if (!gsync(p, gen, &s_flag, bid, G)) return;
     }
 
     // ---- P2: U~ = Z L^-1 = Z Zi^T over 16 x 16 tiles, longest rows of Zi first ------
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     {
         const int D16 = (dim + T16 - 1) / T16, C16 = (R + T16 - 1) / T16;
         const int ntile = D16 * C16;
-        for (int tile = blockIdx.x; tile < ntile; tile += G) {
+        for (int tile = bid; tile < ntile; tile += G) {
             const int cb = tile / D16, xb = tile % D16;
             const int x0 = xb * T16, c0 = cb * T16;
             double acc = 0.0;
@@ -484,12 +485,12 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             if (x0 + ty16 < dim && c0 + tx16 < R) p.U[(long long)(x0 + ty16) * R + c0 + tx16] = acc;
         }
     }
-    if (!gsync(p, gen, &s_flag)) return;
+    if (!gsync(p, gen, &s_flag, bid, G)) return;
 
     // ---- P3: normalise: 32 columns per block, 8 row groups, a zero column keeps lam = 0
     {
         const int c = tid % 32, rg = tid / 32;
-        for (int cb = blockIdx.x; cb * 32 < R; cb += G) {
+        for (int cb = bid; cb * 32 < R; cb += G) {
             const int r = cb * 32 + c;
             double s = 0.0;
             if (r < R)
@@ -514,12 +515,12 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
             __syncthreads();
         }
     }
-    if (!gsync(p, gen, &s_flag)) return;
+    if (!gsync(p, gen, &s_flag, bid, G)) return;
 
     // ---- P4: Gram of the new factor, 16 x 16 tiles of the lower triangle ------------
     const int TR = (R + T16 - 1) / T16;
     const int ntri = TR * (TR + 1) / 2;
-    for (int tile = blockIdx.x; tile < ntri; tile += G) {
+    for (int tile = bid; tile < ntri; tile += G) {
         int I, J;
         tri_index(tile, I, J);
         const int i0 = I * T16, j0 = J * T16;
@@ -544,7 +545,73 @@ __global__ void __launch_bounds__(NT) k_solve(const SolveP p) {
     }
 }
 
+__global__ void __launch_bounds__(NT) k_solve(const __grid_constant__ SolveP p) { solve_body(p, blockIdx.x, gridDim.x); }
+
+// Several instances' mode updates in one cooperative launch: instance k runs on
+// blocks blk0[k] .. blk0[k+1]-1 with its own barrier words, so the instances
+// proceed independently and only share the SMs.
+constexpr int MAX_BATCH = 64;
+struct SolveBatch {
+    int n;
+    int blk0[MAX_BATCH + 1];
+    SolveP p[MAX_BATCH];
+};
+
+__global__ void __launch_bounds__(NT) k_solve_batch(const __grid_constant__ SolveBatch b) {
+    int k = 0;
+    while (k + 1 < b.n && b.blk0[k + 1] <= (int)blockIdx.x) ++k;
+    solve_body(b.p[k], (int)blockIdx.x - b.blk0[k], b.blk0[k + 1] - b.blk0[k]);
+}
+
+// the barrier words and the diagonal maximum of every instance start at zero
+__global__ void k_solve_batch_prep(const __grid_constant__ SolveBatch b) {
+    const int k = threadIdx.x;
+    if (k < b.n) {
+        for (int w = 0; w < 4; ++w) b.p[k].sync[w] = 0u;
+        *b.p[k].maxdiag = 0ull;
+    }
+}
+
 int g_solve_grid = 0;
+
+}  // namespace
+
+namespace {
+
+SolveP to_params(const SolveArgs& a) {
+    SolveP p;
+    p.G1 = a.G1; p.G2 = a.G2; p.G3 = a.G3; p.V = a.V; p.Linv = a.Linv; p.M = a.M; p.Z = a.Z; p.Zi = a.Zi;
+    p.U = a.U; p.lam = a.lam; p.G = a.G;
+    p.sync = a.sync; p.maxdiag = a.maxdiag; p.nclamp = a.nclamp; p.err = a.err; p.R = a.R; p.dim = a.dim;
+    p.withhold = a.withhold;
+    p.wait_ns = a.wait_ns > 0 ? a.wait_ns : BAR_NS;
+    return p;
+}
+
+int sm_total() {
+    if (g_solve_grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) return -1;
+        g_solve_grid = sms;   // one block per SM: the look-ahead block keeps its SM's FP64 pipe
+    }
+    return g_solve_grid;
+}
+
+// blocks one instance can use: enough for the first block step's tiles and panel
+// rows, at least 8, at most one per SM
+int solve_want(int dim, int R, int sms) {
+    const int t0 = (R > NB) ? (R - NB + NB - 1) / NB : 0;
+    const int d = (dim + NB - 1) / NB;
+    int want = t0 * (t0 + 1) / 2 + d * t0 + t0;
+    const int ptask = (R + dim + 7) / 8;
+    if (ptask > want) want = ptask;
+    if (want < 8) want = 8;
+    return want < sms ? want : sms;
+}
+
+int g_batch_per_sm = 0;
 
 }  // namespace
 
@@ -552,32 +619,15 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
                     double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
                     int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s) {
-    if (g_solve_grid == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve, NT, 0);
-        if (sms <= 0 || per <= 0) return -1;
-        g_solve_grid = sms;   // one block per SM: the look-ahead block keeps its SM's FP64 pipe
-    }
-    // small problems take fewer blocks (enough for the first step's tiles and
-    // panel rows), so that several instances' solves can share the GPU
-    const int t0 = (R > NB) ? (R - NB + NB - 1) / NB : 0;
-    const int d = (dim + NB - 1) / NB;
-    int want = t0 * (t0 + 1) / 2 + d * t0 + t0;
-    const int ptask = (R + dim + 7) / 8;
-    if (ptask > want) want = ptask;
-    if (want < 8) want = 8;
-    int grid = want < g_solve_grid ? want : g_solve_grid;
+    const int sms = sm_total();
+    if (sms <= 0) return -1;
+    // small problems take fewer blocks, so that several instances' solves can share the GPU
+    int grid = solve_want(dim, R, sms);
     if (grid_cap > 0 && grid > grid_cap) grid = grid_cap < 8 ? 8 : grid_cap;
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
-    SolveP p;
-    p.G1 = G1; p.G2 = G2; p.G3 = G3; p.V = V; p.Linv = Linv; p.M = M; p.Z = Z; p.Zi = Zi; p.U = U; p.lam = lam;
-    p.G = G;
-    p.sync = sync; p.maxdiag = maxdiag; p.nclamp = nclamp; p.err = err; p.R = R; p.dim = dim;
-    p.withhold = withhold;
-    p.wait_ns = wait_ns > 0 ? wait_ns : BAR_NS;
+    SolveArgs a{G1, G2, G3, M, dim, R, V, Linv, Z, Zi, U, lam, G, sync, maxdiag, nclamp, err, wait_ns, withhold};
+    const SolveP p = to_params(a);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);
@@ -590,4 +640,96 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
     cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve, p);
     return e == cudaSuccess ? 0 : -(1000 + (int)e);
+}
+
+int solve_modes_batched(const SolveArgs* a, int n, cudaStream_t s) {
+    const int sms = sm_total();
+    if (sms <= 0) return -1;
+    if (g_batch_per_sm == 0) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_batch, NT, 0) != cudaSuccess || per <= 0) {
+            cudaGetLastError();
+            return -2;
+        }
+        g_batch_per_sm = per;
+    }
+    const int cap = g_batch_per_sm * sms;   // blocks that are co-resident in one cooperative launch
+    for (int k0 = 0; k0 < n; k0 += MAX_BATCH) {
+        const int nb = (n - k0 < MAX_BATCH) ? n - k0 : MAX_BATCH;
+        if (2 * nb > cap) return -3;
+        SolveBatch b;
+        b.n = nb;
+        int want[MAX_BATCH], alloc[MAX_BATCH];
+        long long total = 0;
+        double wsum = 0.0, work[MAX_BATCH];
+        for (int k = 0; k < nb; ++k) {
+            const SolveArgs& x = a[k0 + k];
+            want[k] = solve_want(x.dim, x.R, sms);
+            total += want[k];
+            work[k] = (double)x.R * x.R * x.R / 3.0 + 4.0 * x.dim * (double)x.R * x.R;
+            wsum += work[k];
+        }
+        if (total <= cap) {
+            for (int k = 0; k < nb; ++k) alloc[k] = want[k];
+        } else {
+            // share the co-resident blocks out by FP64 work, at least 2 per instance
+            const int spare = cap - 2 * nb;
+            long long used = 0;
+            for (int k = 0; k < nb; ++k) {
+                int g = 2 + (int)((double)spare * work[k] / wsum);
+                if (g > want[k]) g = want[k];
+                alloc[k] = g;
+                used += g;
+            }
+            while (used > cap) {   // rounding cannot overshoot, but keep the launch valid regardless
+                int big = 0;
+                for (int k = 1; k < nb; ++k)
+                    if (alloc[k] > alloc[big]) big = k;
+                if (alloc[big] <= 2) return -3;
+                --alloc[big];
+                --used;
+            }
+        }
+        int blk = 0;
+        for (int k = 0; k < nb; ++k) {
+            b.blk0[k] = blk;
+            b.p[k] = to_params(a[k0 + k]);
+            blk += alloc[k];
+        }
+        b.blk0[nb] = blk;
+        k_solve_batch_prep<<<1, MAX_BATCH, 0, s>>>(b);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blk);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_batch, b);
+        if (e != cudaSuccess) return -(1000 + (int)e);
+    }
+    return 0;
+}
+
+// ---- self-test of the pivot reciprocal --------------------------------------
+
+namespace {
+
+__global__ void k_recip_check(const double* d, double* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = recip_nr(d[i]);
+}
+
+}  // namespace
+
+extern "C" int ppl_test_reciprocal(const double* d, double* out, int n, void* stream) {
+    if (!d || !out || n < 0) return 1;   // PPL_EINVAL
+    if (n == 0) return 0;
+    k_recip_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d, out, n);
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return 3;   // PPL_ECUDA
+    return 0;
 }

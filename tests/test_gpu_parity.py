@@ -502,3 +502,33 @@ def test_bounded_wait_expires_and_handle_recovers(use_graph):
     U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 2)
     _check_factors(_factors(cp), U_ref, lam_ref, 2e-4, f"tf32x3 sweeps after a timeout (graph {use_graph})")
     cp.close()
+
+
+def test_pivot_reciprocal_within_two_ulp():
+    """The Cholesky inverts its pivots with the PTX approximate FP64 reciprocal
+    refined by two Newton-Raphson steps (each squares the relative error).  Over
+    a log-spaced sweep of positive normal doubles from 1e-300 to 1e300, values
+    just above and below powers of two, random mantissas, and pivots of the size
+    of the clamp tolerance (2^-52 R max V_kk for R up to 2400), the result is
+    within two ulps of the correctly rounded 1/d."""
+    rng = np.random.default_rng(3)
+    d = [np.logspace(-300, 300, 120001)]
+    e = np.arange(-990, 991, 7, dtype=np.float64)
+    d.append(np.ldexp(1.0, e.astype(int)))
+    d.append(np.nextafter(np.ldexp(1.0, e.astype(int)), 0.0))
+    d.append(np.nextafter(np.ldexp(1.0, e.astype(int)), np.inf))
+    d.append(rng.uniform(1.0, 2.0, 20000) * np.ldexp(1.0, rng.integers(-900, 900, 20000)))
+    d.append(2.0 ** -52 * np.array([1, 48, 800, 1600, 2400], dtype=np.float64)[:, None]
+             * np.logspace(-6, 6, 101)[None, :])
+    d = np.concatenate([x.ravel() for x in d])
+    d = d[(d > 1e-300) & (d < 1e300)]
+    dev = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dev)
+    rc = binding.lib().ppl_test_reciprocal(dev.data_ptr(), out.data_ptr(), dev.numel(),
+                                            torch.cuda.current_stream().cuda_stream)
+    assert rc == binding.PPL_OK
+    got = out.cpu().numpy()
+    ref = 1.0 / d
+    ulps = np.abs(got - ref) / np.spacing(ref)
+    w = int(np.argmax(ulps))
+    assert ulps[w] <= 2.0, (d[w], got[w], ref[w], ulps[w])
