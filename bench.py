@@ -171,19 +171,22 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_from_profile(key: str, prof_name: str = "mttkrp_tc_cfg4_traffic.json", src_name: str = "ppl_tc.cu"):
+def traffic_from_profile(key: str, prof_name: str = "mttkrp_tc_cfg4_traffic.json",
+                         src_names=("ppl_tc.cu", "ppl_cpd.cu")):
     """DRAM bytes per sweep from a committed ncu summary (profiles/<prof_name>)
-    if it was taken on the current source of the kernel; else None."""
-    src = os.path.join(ROOT, "paper_2503_10380_gb300", "csrc", src_name)
+    if it was taken on the current sources of the kernels and their
+    orchestration; else None."""
     prof = os.path.join(ROOT, "profiles", prof_name)
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         d = json.load(open(prof))
-        if d.get(src_name.replace(".cu", "") + "_sha256") == h:
-            return d.get(key)
+        for src_name in src_names:
+            src = os.path.join(ROOT, "paper_2503_10380_gb300", "csrc", src_name)
+            h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            if d.get(src_name.replace(".cu", "") + "_sha256") != h:
+                return None
+        return d.get(key)
     except Exception:
-        pass
-    return None
+        return None
 
 
 def tensor_peak(pk, precision):
@@ -538,12 +541,16 @@ def run_ours(args, world, rank, local):
     peak_tc = pk["tf32_tflops_sustained"] / 3.0
     solve_tflops = fp64_solve_flops(o, v, R) / (solve_ms / 1000.0) / 1e12
     roof_solve = {"bound": "alu", "achieved": solve_tflops, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                  "frac": solve_tflops / pk["fp64_tflops"], "traffic": None, "ms_per_sweep": solve_ms,
+                  "frac": solve_tflops / pk["fp64_tflops"],
+                  "traffic": traffic_from_profile("solve_bytes_per_sweep", src_names=("ppl_solve.cu", "ppl_cpd.cu"))
+                  if MAIN_CFG == (60, 600, 1800, 2400) else None, "ms_per_sweep": solve_ms,
                   "kernel": "k_solve (FP64 mode updates, cooperative, 4 launches per sweep)",
                   "peak_source": "measured in this run: ppl_probe_fp64_peak (FP64 FMA chains on every SM)",
                   "work": "per sweep 4 (R^3/3 + 4 dim R^2) FP64 flops: Cholesky, two triangular solves, Gram"}
     roof_mttkrp = {"bound": "tensor", "achieved": mttkrp_tflops, "peak": peak_tc, "unit": "TFLOP/s",
-                   "frac": mttkrp_tflops / peak_tc, "traffic": traffic_from_profile("mttkrp_bytes_per_sweep"),
+                   "frac": mttkrp_tflops / peak_tc,
+                   "traffic": traffic_from_profile("mttkrp_bytes_per_sweep") if MAIN_CFG == (60, 600, 1800, 2400) else None,
+                   "traffic_unit": "DRAM bytes per sweep (ncu, profiles/mttkrp_tc_cfg4_traffic.json)",
                    "ms_per_sweep": mttkrp_ms,
                    "kernel": "k_tc_gemm and its helpers (all MTTKRP contractions of one sweep)",
                    "peak_source": "measured in this run: sustained TF32 cuBLAS GEMM / 3 (three tf32 MMAs per "
