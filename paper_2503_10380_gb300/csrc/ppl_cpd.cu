@@ -31,7 +31,7 @@ long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
 struct Layout {
     // offsets (bytes) into the workspace; -1 = absent
-    size_t G[4], V, Linv, Z, Zi, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
+    size_t G[4], V, Linv, Z, M, P, scal, partial, hist, flags, KR64, Uold[4], lamold, Xc[4];
     size_t T64, W64, Y64, S64;                       // FP64 form
     size_t tauT, tauN, Bn, Bp, BpW, UopA, UopB, KRT, T, Tt, W, Y, WTa, WTb, S, PART;   // tensor-core form
     size_t Bbar, BbN, BbP, BbT;   // t1-dressed D-bar: FP64 [X][v][v] and its operand layouts
@@ -113,7 +113,6 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
     L.V = take(RR * d);
     L.Linv = take((size_t)((R + 31) / 32) * 32 * 32 * d);
     L.Z = take((size_t)dim * R * d);
-    L.Zi = take(RR * d);
     L.M = take((size_t)dim * R * d);
     L.P = take((size_t)o * o * R * d);
     L.scal = take(NSCAL * d);
@@ -415,7 +414,7 @@ SolveArgs solve_args(ppl_cpd* h, int m) {
     a.M = h->at<double>(h->L.M);
     a.dim = h->dim(m); a.R = h->R;
     a.V = h->at<double>(h->L.V); a.Linv = h->at<double>(h->L.Linv); a.Z = h->at<double>(h->L.Z);
-    a.Zi = h->at<double>(h->L.Zi); a.U = h->U[m]; a.lam = h->lam; a.G = h->G(m);
+    a.U = h->U[m]; a.lam = h->lam; a.G = h->G(m);
     a.sync = reinterpret_cast<unsigned int*>(f + 16);
     a.maxdiag = reinterpret_cast<unsigned long long*>(f + 32);
     a.nclamp = h->nclamp(); a.err = h->errflag();
@@ -426,7 +425,7 @@ SolveArgs solve_args(ppl_cpd* h, int m) {
 // solve the normal equations of mode m from M (in L.M), update U[m], lam, G[m]
 int solve_mode(ppl_cpd* h, int m) {
     const SolveArgs a = solve_args(h, m);
-    const int r = solve_mode_coop(a.G1, a.G2, a.G3, a.M, a.dim, a.R, a.V, a.Linv, a.Z, a.Zi, a.U, a.lam, a.G, a.sync,
+    const int r = solve_mode_coop(a.G1, a.G2, a.G3, a.M, a.dim, a.R, a.V, a.Linv, a.Z, a.U, a.lam, a.G, a.sync,
                                   a.maxdiag, a.nclamp, a.err, h->solve_cap, a.wait_ns, a.withhold, h->st);
     if (r != 0)
         return fail(h, PPL_ECUDA, "cooperative solve launch failed (%d%s%s)", r, r <= -1000 ? ": " : "",

@@ -35,12 +35,12 @@ void hadamard3(const double* G1, const double* G2, const double* G3, int R, doub
 // One mode update in one cooperative launch (ppl_solve.cu): V = G1.G2.G3, clamped
 // Cholesky, U~ = M V^-1, U = U~ / lam, G = U^T U.  Workspace: V [R][R], Linv
 // [ceil(R/32)][32][32] (per diagonal block L[i][j] / L[j][j] below the diagonal and
-// 1 / L[i][i] on it), Z [dim][R], Zi [R][R]; sync (4 words) and maxdiag are reset here.
+// 1 / L[i][i] on it), Z [dim][R]; sync (4 words) and maxdiag are reset here.
 // grid_cap > 0 limits the cooperative grid (so that several solves can share the GPU).
 // wait_ns > 0 bounds every barrier wait (default 1 s); *withhold != 0 makes one
 // block skip its first barrier arrival once (the test of the bounded waits).
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
-                    double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
+                    double* V, double* Linv, double* Z, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
                     int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s);
 // The same mode update for several instances in one cooperative launch (at most
@@ -49,7 +49,7 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
 struct SolveArgs {
     const double *G1, *G2, *G3, *M;
     int dim, R;
-    double *V, *Linv, *Z, *Zi, *U, *lam, *G;
+    double *V, *Linv, *Z, *U, *lam, *G;
     unsigned int* sync;
     unsigned long long *maxdiag, *nclamp;
     unsigned int* err;

@@ -3,15 +3,16 @@
 // three Gram matrices, a Cholesky solve of the normal equations, column
 // normalisation; then the new factor's Gram matrix for the next updates).
 //
-//   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, Zi = I, tol = max(2^-52 R max V_kk, 1e-300)
+//   P0  V = G1 .* G2 .* G3 (lower triangle), Z = M, tol = max(2^-52 R max V_kk, 1e-300)
 //   P1  right-looking blocked Cholesky of V (32-wide blocks, pivots clamped at tol;
 //       panels by warp-per-row triangular solves with the column-scaled diagonal block)
-//       with the rows of Z and of Zi appended below V, so the same panel and
-//       trailing updates carry out the forward substitutions Z <- M L^-T and
-//       Zi <- L^-T (only the block rows of Zi that are already non-zero are updated);
-//       the next diagonal block is updated by three blocks (one lower quarter
-//       each) and factored by block 0 while the others update the rest
-//   P2  U~ = Z L^-1 = Z Zi^T as one product over 16 x 16 output tiles
+//       with the rows of Z appended below V, so the same panel and trailing updates
+//       carry out the forward substitution Z <- M L^-T; the next diagonal block is
+//       updated by three blocks (one lower quarter each) and factored by block 0
+//       while the others update the rest
+//   P2  back substitution U~ L = Z: the rows are independent, so every block solves
+//       its own rows over all column blocks with no grid barrier (one warp per
+//       column block in turn, all eight warps for the updates left of it)
 //   P3  lam_r = ||U~[:, r]||, U = U~ / lam (a zero column keeps lam = 0)
 //   P4  G = U^T U
 //
@@ -38,7 +39,6 @@ struct SolveP {
     double* Linv;
     const double* M;
     double* Z;
-    double* Zi;
     double* U;
     double* lam;
     double* G;
@@ -237,6 +237,87 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
     __syncthreads();
 }
 
+constexpr int RB = 4;   // rows of U~ per back-substitution pass
+
+// Zl[r][c + 8 NB b] -= sum_q x[r][q] L[j0 + q][lane + c + 8 NB b] for the NR rows
+// and CB column blocks b of one warp (Zl and Ll point at the lane's column: Zl at
+// Z[r0][lane], Ll at L[j0][lane])
+template <int NR, int CB>
+__device__ __forceinline__ void back_update(double* Zl, int R, const double* Ll, const double (*x)[NB], int c,
+                                            int kb) {
+    constexpr int BS = (NT / 32) * NB;   // columns between a warp's consecutive blocks
+    double acc[CB][NR];
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[b][r] = __ldcg(Zl + (long long)r * R + c + b * BS);
+#pragma unroll 4
+    for (int q = 0; q < kb; ++q) {
+        double l[CB];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) l[b] = __ldcg(Ll + (long long)q * R + c + b * BS);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const double xv = x[r][q];
+#pragma unroll
+            for (int b = 0; b < CB; ++b) acc[b][r] = fma(-xv, l[b], acc[b][r]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) Zl[(long long)r * R + c + b * BS] = acc[b][r];
+}
+
+// Rows r0 .. r0+NR-1 of the back substitution U~ L = Z, all NT threads of the
+// block.  Warp w owns the 32-column blocks J = w (mod 8).  Column blocks are taken
+// from the last one down: the owner of block J finishes the block's unknowns with
+// the column-scaled diagonal block (x_q is final once the columns right of q are
+// subtracted; then w_t -= x_q L_qt / L_tt for t < q), publishes them, and every
+// warp subtracts x_J L[rows of J][c] from its own columns c left of the block.
+// Block J - 1 belongs to one warp, which applied every earlier update to it
+// itself, so one block barrier per step suffices; the published values alternate
+// between two buffers.
+template <int NR>
+__device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB]) {
+    constexpr int NW = NT / 32;
+    const int R = p.R;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nt = (R + NB - 1) / NB;
+    double* Zr = p.Z + (long long)r0 * R;
+    for (int J = nt - 1; J >= 0; --J) {
+        const int j0 = J * NB, kb = min(NB, R - j0);
+        double (*x)[NB] = xs[J & 1];
+        if (J % NW == warp) {
+            const double* Lj = p.Linv + (long long)J * NB * NB;
+            const double dinv = (lane < kb) ? __ldcg(Lj + lane * NB + lane) : 0.0;
+            double w[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) w[r] = (lane < kb) ? __ldcg(Zr + (long long)r * R + j0 + lane) * dinv : 0.0;
+            for (int q = kb - 1; q > 0; --q) {
+                const double lq = (lane < q) ? __ldcg(Lj + q * NB + lane) : 0.0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) w[r] = fma(-__shfl_sync(0xffffffffu, w[r], q), lq, w[r]);
+            }
+            if (lane < kb) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    x[r][lane] = w[r];
+                    p.U[(long long)(r0 + r) * R + j0 + lane] = w[r];
+                }
+            }
+        }
+        __syncthreads();
+        const double* Ll = p.V + (long long)j0 * R + lane;     // L[j0 + q][lane + c] at q * R + c
+        // CB of the warp's column blocks per pass, so that a pass keeps 4 sums and
+        // CB loads per step of q in flight also when NR is small
+        constexpr int CB = (NR == 1) ? 4 : (NR == 2 ? 2 : 1);
+        int Jc = warp;
+        for (; Jc + NW * (CB - 1) < J; Jc += NW * CB) back_update<NR, CB>(Zr + lane, R, Ll, x, Jc * NB, kb);
+        for (; Jc < J; Jc += NW) back_update<NR, 1>(Zr + lane, R, Ll, x, Jc * NB, kb);
+    }
+}
+
 // One mode update of one instance, run by blocks bid = 0 .. G-1 (of one launch,
 // or of one instance's share of a batched launch); the barriers count G blocks.
 __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const int G) {
@@ -281,7 +362,6 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
         if (q <= r && !(r < kb0 && q < kb0)) p.V[e] = p.G1[e] * p.G2[e] * p.G3[e];
     }
     for (long long e = gtid; e < (long long)dim * R; e += gthreads) p.Z[e] = p.M[e];
-    for (long long e = gtid; e < (long long)R * R; e += gthreads) p.Zi[e] = (e / R == e % R) ? 1.0 : 0.0;
     if (bid == 0) {
         // the first diagonal block straight from the Gram matrices
         for (int e = tid; e < kb0 * kb0; e += NT) {
@@ -307,7 +387,7 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
         __syncthreads();
         // panel: rows below the block (V) and all rows of Z, 8 rows per task
         const int vrows = R - k0 - kb;
-        const int prow = vrows + dim + k0 + kb;      // V rows below the block, Z rows, Zi rows of blocks <= k
+        const int prow = vrows + dim;                // V rows below the block, then the rows of Z
         // one warp per row solves x L^T = a: with val_q final, x_q = val_q / L_qq
         // and val_t -= val_q (L_tq / L_qq), so each column costs one FMA
         const int ntask = (prow + 7) / 8;
@@ -316,10 +396,8 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
             double* row = nullptr;
             if (rr < vrows)
                 row = p.V + (long long)(k0 + kb + rr) * R + k0;
-            else if (rr < vrows + dim)
-                row = p.Z + (long long)(rr - vrows) * R + k0;
             else if (rr < prow)
-                row = p.Zi + (long long)(rr - vrows - dim) * R + k0;
+                row = p.Z + (long long)(rr - vrows) * R + k0;
             if (row) {   // warp-uniform: rr is the same for the 32 lanes
                 double val = (t < kb) ? __ldcg(row + t) : 0.0;
                 for (int q = 0; q < kb; ++q) {
@@ -335,8 +413,7 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
         // blocks take the remaining tiles.
         const int Tk = (vrows + NB - 1) / NB;
         const int ntri = Tk * (Tk + 1) / 2;
-        const int nz = ntri + D * Tk;
-        const int ntile = nz + (k + 1) * Tk;
+        const int ntile = ntri + D * Tk;
         // With three or more blocks, tile 0 (the next diagonal block) is split:
         // blocks 0, 1, 2 each update one of its three lower 16 x 16 quarters,
         // blocks 1 and 2 then signal block 0, which factors the block once both
@@ -411,7 +488,7 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
                 Pa = p.V + (long long)i0 * R + k0;
                 arows = R - i0;
                 C = p.V + (long long)i0 * R + j0;
-            } else if (tile < nz) {
+            } else {
                 const int tz = tile - ntri;
                 const int Mb = tz / Tk, J = tz % Tk;
                 i0 = Mb * NB;
@@ -419,14 +496,6 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
                 Pa = p.Z + (long long)i0 * R + k0;
                 arows = dim - i0;
                 C = p.Z + (long long)i0 * R + j0;
-            } else {
-                const int tz = tile - nz;
-                const int Ib = tz / Tk, J = tz % Tk;
-                i0 = Ib * NB;
-                j0 = k0 + kb + J * NB;
-                Pa = p.Zi + (long long)i0 * R + k0;
-                arows = min(NB, k0 + kb - i0);
-                C = p.Zi + (long long)i0 * R + j0;
             }
             const int brows = R - j0;
             const double* Pb = p.V + (long long)j0 * R + k0;
@@ -460,31 +529,22 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
         if (!gsync(p, gen, &s_flag, bid, G)) return;
     }
 
-    // ---- P2: U~ = Z L^-1 = Z Zi^T over 16 x 16 tiles, longest rows of Zi first ------
-    constexpr int T16 = 16;
-    const int ty16 = tid / T16, tx16 = tid % T16;
+    // ---- P2: back substitution U~ L = Z, RB rows at a time ------------------------
     {
-        const int D16 = (dim + T16 - 1) / T16, C16 = (R + T16 - 1) / T16;
-        const int ntile = D16 * C16;
-        for (int tile = bid; tile < ntile; tile += G) {
-            const int cb = tile / D16, xb = tile % D16;
-            const int x0 = xb * T16, c0 = cb * T16;
-            double acc = 0.0;
-            for (int s0 = c0; s0 < R; s0 += NB) {     // Zi[c][s] = 0 for s < c
-                for (int e = tid; e < T16 * NB; e += NT) {
-                    const int i = e / NB, j = e % NB;
-                    const bool oks = (s0 + j < R);
-                    Ta[i][j] = (oks && x0 + i < dim) ? __ldcg(p.Z + (long long)(x0 + i) * R + s0 + j) : 0.0;
-                    Tb[i][j] = (oks && c0 + i < R) ? __ldcg(p.Zi + (long long)(c0 + i) * R + s0 + j) : 0.0;
-                }
-                __syncthreads();
-#pragma unroll 8
-                for (int j = 0; j < NB; ++j) acc = fma(Ta[ty16][j], Tb[tx16][j], acc);
-                __syncthreads();
+        __shared__ double xs[2][RB][NB];
+        const int rpc = (dim + G - 1) / G;
+        const int rbeg = bid * rpc, rend = min(dim, rbeg + rpc);
+        for (int r0 = rbeg; r0 < rend; r0 += RB) {
+            switch (min(RB, rend - r0)) {
+                case 4: back_rows<4>(p, r0, xs); break;
+                case 3: back_rows<3>(p, r0, xs); break;
+                case 2: back_rows<2>(p, r0, xs); break;
+                default: back_rows<1>(p, r0, xs); break;
             }
-            if (x0 + ty16 < dim && c0 + tx16 < R) p.U[(long long)(x0 + ty16) * R + c0 + tx16] = acc;
         }
     }
+    constexpr int T16 = 16;
+    const int ty16 = tid / T16, tx16 = tid % T16;
     if (!gsync(p, gen, &s_flag, bid, G)) return;
 
     // ---- P3: normalise: 32 columns per block, 8 row groups, a zero column keeps lam = 0
@@ -557,7 +617,7 @@ struct SolveBatch {
     SolveP p[MAX_BATCH];
 };
 
-__global__ void __launch_bounds__(NT) k_solve_batch(const __grid_constant__ SolveBatch b) {
+__global__ void __launch_bounds__(NT, 3) k_solve_batch(const __grid_constant__ SolveBatch b) {
     int k = 0;
     while (k + 1 < b.n && b.blk0[k + 1] <= (int)blockIdx.x) ++k;
     solve_body(b.p[k], (int)blockIdx.x - b.blk0[k], b.blk0[k + 1] - b.blk0[k]);
@@ -580,7 +640,7 @@ namespace {
 
 SolveP to_params(const SolveArgs& a) {
     SolveP p;
-    p.G1 = a.G1; p.G2 = a.G2; p.G3 = a.G3; p.V = a.V; p.Linv = a.Linv; p.M = a.M; p.Z = a.Z; p.Zi = a.Zi;
+    p.G1 = a.G1; p.G2 = a.G2; p.G3 = a.G3; p.V = a.V; p.Linv = a.Linv; p.M = a.M; p.Z = a.Z;
     p.U = a.U; p.lam = a.lam; p.G = a.G;
     p.sync = a.sync; p.maxdiag = a.maxdiag; p.nclamp = a.nclamp; p.err = a.err; p.R = a.R; p.dim = a.dim;
     p.withhold = a.withhold;
@@ -604,7 +664,7 @@ int sm_total() {
 int solve_want(int dim, int R, int sms) {
     const int t0 = (R > NB) ? (R - NB + NB - 1) / NB : 0;
     const int d = (dim + NB - 1) / NB;
-    int want = t0 * (t0 + 1) / 2 + d * t0 + t0;
+    int want = t0 * (t0 + 1) / 2 + d * t0;
     const int ptask = (R + dim + 7) / 8;
     if (ptask > want) want = ptask;
     if (want < 8) want = 8;
@@ -616,7 +676,7 @@ int g_batch_per_sm = 0;
 }  // namespace
 
 int solve_mode_coop(const double* G1, const double* G2, const double* G3, const double* M, int dim, int R,
-                    double* V, double* Linv, double* Z, double* Zi, double* U, double* lam, double* G,
+                    double* V, double* Linv, double* Z, double* U, double* lam, double* G,
                     unsigned int* sync, unsigned long long* maxdiag, unsigned long long* nclamp, unsigned int* err,
                     int grid_cap, unsigned long long wait_ns, unsigned int* withhold, cudaStream_t s) {
     const int sms = sm_total();
@@ -626,7 +686,7 @@ int solve_mode_coop(const double* G1, const double* G2, const double* G3, const 
     if (grid_cap > 0 && grid > grid_cap) grid = grid_cap < 8 ? 8 : grid_cap;
     cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned int), s);
     cudaMemsetAsync(maxdiag, 0, sizeof(unsigned long long), s);
-    SolveArgs a{G1, G2, G3, M, dim, R, V, Linv, Z, Zi, U, lam, G, sync, maxdiag, nclamp, err, wait_ns, withhold};
+    SolveArgs a{G1, G2, G3, M, dim, R, V, Linv, Z, U, lam, G, sync, maxdiag, nclamp, err, wait_ns, withhold};
     const SolveP p = to_params(a);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
