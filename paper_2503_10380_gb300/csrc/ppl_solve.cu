@@ -117,8 +117,9 @@ __device__ bool gsync(const SolveP& p, unsigned int& gen, int* s_flag, int bid, 
 }
 
 __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
-    // t -> (I, J), I >= J, row-major over the lower triangle
-    int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    // t -> (I, J), I >= J, row-major over the lower triangle (an FP32 estimate,
+    // corrected exactly below: the FP64 pipe is the solve's bottleneck)
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= t) ++i;
     while (i * (i + 1) / 2 > t) --i;
     I = i;
@@ -239,6 +240,20 @@ __device__ void factor_block(const SolveP& p, int k, double tol, double (*Ls)[NB
 
 constexpr int RB = 4;   // rows of U~ per back-substitution pass
 
+// asynchronous global -> shared copies (cp.async), waited for by the issuing thread
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// one warp copies an NB x NB block (row-major, NB doubles per row) into dst
+__device__ __forceinline__ void stage_block(const double* src, double (*dst)[NB + 1], int lane) {
+#pragma unroll 8
+    for (int q = 0; q < NB; ++q) cp_async8(&dst[q][lane], src + q * NB + lane);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // Zl[r][c + 8 NB b] -= sum_q x[r][q] L[j0 + q][lane + c + 8 NB b] for the NR rows
 // and CB column blocks b of one warp (Zl and Ll point at the lane's column: Zl at
 // Z[r0][lane], Ll at L[j0][lane])
@@ -279,23 +294,26 @@ __device__ __forceinline__ void back_update(double* Zl, int R, const double* Ll,
 // itself, so one block barrier per step suffices; the published values alternate
 // between two buffers.
 template <int NR>
-__device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB]) {
+__device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB], double (*lb0)[NB + 1], double (*lb1)[NB + 1]) {
     constexpr int NW = NT / 32;
     const int R = p.R;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nt = (R + NB - 1) / NB;
     double* Zr = p.Z + (long long)r0 * R;
+    if ((nt - 1) % NW == warp) stage_block(p.Linv + (long long)(nt - 1) * NB * NB, ((nt - 1) & 1) ? lb1 : lb0, lane);
     for (int J = nt - 1; J >= 0; --J) {
         const int j0 = J * NB, kb = min(NB, R - j0);
         double (*x)[NB] = xs[J & 1];
         if (J % NW == warp) {
-            const double* Lj = p.Linv + (long long)J * NB * NB;
-            const double dinv = (lane < kb) ? __ldcg(Lj + lane * NB + lane) : 0.0;
+            cp_async_wait_all();
+            __syncwarp();
+            const double (*Ld)[NB + 1] = (J & 1) ? lb1 : lb0;
+            const double dinv = (lane < kb) ? Ld[lane][lane] : 0.0;
             double w[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = (lane < kb) ? __ldcg(Zr + (long long)r * R + j0 + lane) * dinv : 0.0;
             for (int q = kb - 1; q > 0; --q) {
-                const double lq = (lane < q) ? __ldcg(Lj + q * NB + lane) : 0.0;
+                const double lq = (lane < q) ? Ld[q][lane] : 0.0;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) w[r] = fma(-__shfl_sync(0xffffffffu, w[r], q), lq, w[r]);
             }
@@ -308,6 +326,8 @@ __device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB]) {
             }
         }
         __syncthreads();
+        // the owner of the next block stages its diagonal block during this step
+        if (J > 0 && (J - 1) % NW == warp) stage_block(p.Linv + (long long)(J - 1) * NB * NB, ((J - 1) & 1) ? lb1 : lb0, lane);
         const double* Ll = p.V + (long long)j0 * R + lane;     // L[j0 + q][lane + c] at q * R + c
         // CB of the warp's column blocks per pass, so that a pass keeps 4 sums and
         // CB loads per step of q in flight also when NR is small
@@ -315,6 +335,81 @@ __device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB]) {
         int Jc = warp;
         for (; Jc + NW * (CB - 1) < J; Jc += NW * CB) back_update<NR, CB>(Zr + lane, R, Ll, x, Jc * NB, kb);
         for (; Jc < J; Jc += NW) back_update<NR, 1>(Zr + lane, R, Ll, x, Jc * NB, kb);
+    }
+}
+
+// One 32 x 32 tile of a block step's trailing update: C -= Pa Pb^T over the kb
+// columns of the panel, C in the lower triangle of V (tiles below the next
+// diagonal) or in Z (the appended rows).
+struct TrailTile {
+    const double* Pa;
+    const double* Pb;
+    double* C;
+    int arows, brows;
+    bool diag;      // a diagonal tile of V: only j <= i is updated
+};
+
+__device__ __forceinline__ TrailTile trail_tile(const SolveP& p, int tile, int k0, int kb, int ntri, int Tk, int dim) {
+    const int R = p.R;
+    TrailTile t;
+    int i0, j0;
+    if (tile < ntri) {
+        int I, J;
+        tri_index(tile, I, J);
+        i0 = k0 + kb + I * NB;
+        j0 = k0 + kb + J * NB;
+        t.Pa = p.V + (long long)i0 * R + k0;
+        t.arows = R - i0;
+        t.C = p.V + (long long)i0 * R + j0;
+        t.diag = (I == J);
+    } else {
+        const int tz = tile - ntri;
+        const int Mb = tz / Tk, J = tz % Tk;
+        i0 = Mb * NB;
+        j0 = k0 + kb + J * NB;
+        t.Pa = p.Z + (long long)i0 * R + k0;
+        t.arows = dim - i0;
+        t.C = p.Z + (long long)i0 * R + j0;
+        t.diag = false;
+    }
+    t.brows = R - j0;
+    t.Pb = p.V + (long long)j0 * R + k0;
+    return t;
+}
+
+__device__ __forceinline__ bool trail_owns(const TrailTile& t, int i, int j) {
+    return i < t.arows && j < t.brows && (!t.diag || j <= i);
+}
+
+// this thread's four elements of each operand tile and its four C values
+__device__ __forceinline__ void trail_fetch(const TrailTile& t, int R, int kb, int tid, int tx, int ty, double* pa,
+                                            double* pb, double* pc) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = tid + u * NT;
+        const int i = e / NB, s2 = e % NB;
+        pa[u] = (i < t.arows && s2 < kb) ? __ldcg(t.Pa + (long long)i * R + s2) : 0.0;
+        pb[u] = (i < t.brows && s2 < kb) ? __ldcg(t.Pb + (long long)i * R + s2) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = ty + 16 * (u >> 1), j = tx + 16 * (u & 1);
+        pc[u] = trail_owns(t, i, j) ? __ldcg(t.C + (long long)i * R + j) : 0.0;
+    }
+}
+
+// this thread's two elements of each 32 x 16 operand of the Gram tile at (i0, j0)
+// (16 x 16 tiles of the lower triangle), rows x0 .. x0+31 of U
+__device__ __forceinline__ void gram_fetch(const SolveP& p, int i0, int j0, int x0, int tid, double* qa, double* qb) {
+    constexpr int T16 = 16;
+    const int R = p.R, dim = p.dim;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int e = tid + u * NT;
+        const int x = e / T16, c = e % T16;
+        const bool okx = (x0 + x < dim);
+        qa[u] = (okx && i0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + i0 + c) : 0.0;
+        qb[u] = (okx && j0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + j0 + c) : 0.0;
     }
 }
 
@@ -475,36 +570,30 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
             first = bid;
             stride = G - 1;
         }
-        for (int tile = first; tile < ntile; tile += stride) {
-            const double* Pa;
-            int arows, i0;
-            double* C;
-            int j0;
-            if (tile < ntri) {
-                int I, J;
-                tri_index(tile, I, J);
-                i0 = k0 + kb + I * NB;
-                j0 = k0 + kb + J * NB;
-                Pa = p.V + (long long)i0 * R + k0;
-                arows = R - i0;
-                C = p.V + (long long)i0 * R + j0;
-            } else {
-                const int tz = tile - ntri;
-                const int Mb = tz / Tk, J = tz % Tk;
-                i0 = Mb * NB;
-                j0 = k0 + kb + J * NB;
-                Pa = p.Z + (long long)i0 * R + k0;
-                arows = dim - i0;
-                C = p.Z + (long long)i0 * R + j0;
+        // each block's tiles in turn; the operands and the C values of the next
+        // tile are loaded into registers while the current one is multiplied
+        TrailTile cur{}, nxt{};
+        double pa[4], pb[4], pc[4];
+        int tile = first;
+        if (tile < ntile) {
+            cur = trail_tile(p, tile, k0, kb, ntri, Tk, dim);
+            trail_fetch(cur, R, kb, tid, tx, ty, pa, pb, pc);
+        }
+        for (; tile < ntile; tile += stride) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = tid + u * NT;
+                Ta[e / NB][e % NB] = pa[u];
+                Tb[e / NB][e % NB] = pb[u];
             }
-            const int brows = R - j0;
-            const double* Pb = p.V + (long long)j0 * R + k0;
-            for (int e = tid; e < NB * NB; e += NT) {
-                const int i = e / NB, s2 = e % NB;
-                Ta[i][s2] = (i < arows && s2 < kb) ? __ldcg(Pa + (long long)i * R + s2) : 0.0;
-                Tb[i][s2] = (i < brows && s2 < kb) ? __ldcg(Pb + (long long)i * R + s2) : 0.0;
-            }
+            double c4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c4[u] = pc[u];
             __syncthreads();
+            if (tile + stride < ntile) {
+                nxt = trail_tile(p, tile + stride, k0, kb, ntri, Tk, dim);
+                trail_fetch(nxt, R, kb, tid, tx, ty, pa, pb, pc);
+            }
             double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
             for (int s2 = 0; s2 < kb; ++s2) {
                 const double x0 = Ta[ty][s2], x1 = Ta[ty + 16][s2];
@@ -514,17 +603,15 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
                 a10 = fma(x1, y0, a10);
                 a11 = fma(x1, y1, a11);
             }
-            const double acc[2][2] = {{a00, a01}, {a10, a11}};
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b) {
-                    const int i = ty + 16 * a, j = tx + 16 * b;
-                    if (i < arows && j < brows && (tile >= ntri || i0 != j0 || j <= i)) {
-                        double* c = C + (long long)i * R + j;
-                        *c = __ldcg(c) - acc[a][b];
-                    }
-                }
+            const double acc[4] = {a00, a01, a10, a11};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = ty + 16 * (u >> 1), j = tx + 16 * (u & 1);
+                if (trail_owns(cur, i, j)) cur.C[(long long)i * R + j] = c4[u] - acc[u];
+            }
             __syncthreads();
             if (tile == 0 && k + 1 < nt && !split0) factor_block(p, k + 1, tol, Ls, Li, rd, tri, Tb);
+            cur = nxt;
         }
         if (!gsync(p, gen, &s_flag, bid, G)) return;
     }
@@ -536,10 +623,10 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
         const int rbeg = bid * rpc, rend = min(dim, rbeg + rpc);
         for (int r0 = rbeg; r0 < rend; r0 += RB) {
             switch (min(RB, rend - r0)) {
-                case 4: back_rows<4>(p, r0, xs); break;
-                case 3: back_rows<3>(p, r0, xs); break;
-                case 2: back_rows<2>(p, r0, xs); break;
-                default: back_rows<1>(p, r0, xs); break;
+                case 4: back_rows<4>(p, r0, xs, Ls, Li); break;
+                case 3: back_rows<3>(p, r0, xs, Ls, Li); break;
+                case 2: back_rows<2>(p, r0, xs, Ls, Li); break;
+                default: back_rows<1>(p, r0, xs, Ls, Li); break;
             }
         }
     }
@@ -580,32 +667,62 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
     // ---- P4: Gram of the new factor, 16 x 16 tiles of the lower triangle ------------
     const int TR = (R + T16 - 1) / T16;
     const int ntri = TR * (TR + 1) / 2;
-    for (int tile = bid; tile < ntri; tile += G) {
-        int I, J;
-        tri_index(tile, I, J);
-        const int i0 = I * T16, j0 = J * T16;
+    // each block's (tile, 32-row step) pairs in turn, the next pair's operands
+    // loaded into registers while the current one is multiplied
+    {
+        const int nx = (dim + NB - 1) / NB;
+        int tile = bid, xs = 0;
+        int ti0 = 0, tj0 = 0;              // the current tile's corner
+        if (tile < ntri) {
+            int I, J;
+            tri_index(tile, I, J);
+            ti0 = I * T16;
+            tj0 = J * T16;
+        }
+        int ni0 = ti0, nj0 = tj0;          // the next pair's tile corner
+        double qa[2], qb[2];
+        if (tile < ntri) gram_fetch(p, ti0, tj0, 0, tid, qa, qb);
         double acc = 0.0;
-        for (int x0 = 0; x0 < dim; x0 += NB) {
-            for (int e = tid; e < NB * T16; e += NT) {
-                const int x = e / T16, c = e % T16;
-                const bool okx = (x0 + x < dim);
-                Ta[x][c] = (okx && i0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + i0 + c) : 0.0;
-                Tb[x][c] = (okx && j0 + c < R) ? __ldcg(p.U + (long long)(x0 + x) * R + j0 + c) : 0.0;
+        while (tile < ntri) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = tid + u * NT;
+                Ta[e / T16][e % T16] = qa[u];
+                Tb[e / T16][e % T16] = qb[u];
             }
             __syncthreads();
+            int ntl = tile, nxs = xs + 1;
+            if (nxs == nx) {
+                ntl += G;
+                nxs = 0;
+                if (ntl < ntri) {
+                    int I, J;
+                    tri_index(ntl, I, J);
+                    ni0 = I * T16;
+                    nj0 = J * T16;
+                }
+            }
+            if (ntl < ntri) gram_fetch(p, ni0, nj0, nxs * NB, tid, qa, qb);
 #pragma unroll 8
             for (int x = 0; x < NB; ++x) acc = fma(Ta[x][ty16], Tb[x][tx16], acc);
             __syncthreads();
-        }
-        const int i = i0 + ty16, j = j0 + tx16;
-        if (i < R && j < R) {
-            p.G[(long long)i * R + j] = acc;
-            p.G[(long long)j * R + i] = acc;
+            if (nxs == 0) {
+                const int i = ti0 + ty16, j = tj0 + tx16;
+                if (i < R && j < R) {
+                    p.G[(long long)i * R + j] = acc;
+                    p.G[(long long)j * R + i] = acc;
+                }
+                acc = 0.0;
+            }
+            tile = ntl;
+            xs = nxs;
+            ti0 = ni0;
+            tj0 = nj0;
         }
     }
 }
 
-__global__ void __launch_bounds__(NT) k_solve(const __grid_constant__ SolveP p) { solve_body(p, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(NT, 1) k_solve(const __grid_constant__ SolveP p) { solve_body(p, blockIdx.x, gridDim.x); }
 
 // Several instances' mode updates in one cooperative launch: instance k runs on
 // blocks blk0[k] .. blk0[k+1]-1 with its own barrier words, so the instances
