@@ -254,23 +254,22 @@ __device__ __forceinline__ void stage_block(const double* src, double (*dst)[NB 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Zl[r][c + 8 NB b] -= sum_q x[r][q] L[j0 + q][lane + c + 8 NB b] for the NR rows
-// and CB column blocks b of one warp (Zl and Ll point at the lane's column: Zl at
-// Z[r0][lane], Ll at L[j0][lane])
-template <int NR, int CB>
-__device__ __forceinline__ void back_update(double* Zl, int R, const double* Ll, const double (*x)[NB], int c,
-                                            int kb) {
-    constexpr int BS = (NT / 32) * NB;   // columns between a warp's consecutive blocks
-    double acc[CB][NR];
+// Zl[r][c + bs b] -= sum_q x[r][q] L[j0 + q][lane + c + bs b] for the NR rows and
+// CB column blocks b of one warp (Zl and Ll point at the lane's column: Zl at
+// Z[r0][lane], Ll at L[j0][lane]).  KEEP: one block, the result returned in acc
+// instead of stored.
+template <int NR, int CB, bool KEEP = false>
+__device__ __forceinline__ void back_update(double* Zl, int R, const double* Ll, const double (*x)[NB], int c, int kb,
+                                            int bs, double (*acc)[NR]) {
 #pragma unroll
     for (int b = 0; b < CB; ++b)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[b][r] = __ldcg(Zl + (long long)r * R + c + b * BS);
+        for (int r = 0; r < NR; ++r) acc[b][r] = __ldcg(Zl + (long long)r * R + c + b * bs);
 #pragma unroll 4
     for (int q = 0; q < kb; ++q) {
         double l[CB];
 #pragma unroll
-        for (int b = 0; b < CB; ++b) l[b] = __ldcg(Ll + (long long)q * R + c + b * BS);
+        for (int b = 0; b < CB; ++b) l[b] = __ldcg(Ll + (long long)q * R + c + b * bs);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const double xv = x[r][q];
@@ -278,63 +277,95 @@ __device__ __forceinline__ void back_update(double* Zl, int R, const double* Ll,
             for (int b = 0; b < CB; ++b) acc[b][r] = fma(-xv, l[b], acc[b][r]);
         }
     }
+    if (!KEEP) {
 #pragma unroll
-    for (int b = 0; b < CB; ++b)
+        for (int b = 0; b < CB; ++b)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) Zl[(long long)r * R + c + b * BS] = acc[b][r];
+            for (int r = 0; r < NR; ++r) Zl[(long long)r * R + c + b * bs] = acc[b][r];
+    }
+}
+
+// The kb unknowns of one column block for NR rows (one warp, lane = column):
+// w holds the block of Z with every block to its right already subtracted; with
+// the column-scaled diagonal block Ld (L_qt / L_tt below the diagonal, 1 / L_tt
+// on it), x_q is final once the columns right of q are subtracted, then
+// w_t -= x_q L_qt / L_tt for t < q.
+template <int NR>
+__device__ __forceinline__ void back_diag(const double (*Ld)[NB + 1], int kb, int lane, double* w) {
+    const double dinv = (lane < kb) ? Ld[lane][lane] : 0.0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r] = (lane < kb) ? w[r] * dinv : 0.0;
+    for (int q = kb - 1; q > 0; --q) {
+        const double lq = (lane < q) ? Ld[q][lane] : 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) w[r] = fma(-__shfl_sync(0xffffffffu, w[r], q), lq, w[r]);
+    }
 }
 
 // Rows r0 .. r0+NR-1 of the back substitution U~ L = Z, all NT threads of the
-// block.  Warp w owns the 32-column blocks J = w (mod 8).  Column blocks are taken
-// from the last one down: the owner of block J finishes the block's unknowns with
-// the column-scaled diagonal block (x_q is final once the columns right of q are
-// subtracted; then w_t -= x_q L_qt / L_tt for t < q), publishes them, and every
-// warp subtracts x_J L[rows of J][c] from its own columns c left of the block.
-// Block J - 1 belongs to one warp, which applied every earlier update to it
-// itself, so one block barrier per step suffices; the published values alternate
-// between two buffers.
+// block, column blocks from the last one down.  At step J the unknowns x_J are
+// published in shared memory; warp (J-1) mod 8 subtracts x_J L[rows of J][block
+// J-1] from block J-1, keeps the result in registers and solves it at once
+// (x_{J-1}), while the seven other warps subtract x_J from blocks 0 .. J-2; one
+// block barrier per step.  The diagonal block of J-1 was copied to shared memory
+// (cp.async) by the same warp one step earlier; the published values and the
+// staged blocks alternate between two buffers.
 template <int NR>
 __device__ void back_rows(const SolveP& p, int r0, double (*xs)[RB][NB], double (*lb0)[NB + 1], double (*lb1)[NB + 1]) {
-    constexpr int NW = NT / 32;
+    constexpr int NW = NT / 32, NO = NW - 1;
+    // CB blocks per pass, so that a pass keeps 4 sums and CB loads per step of q
+    // in flight also when NR is small
+    constexpr int CB = (NR == 1) ? 4 : (NR == 2 ? 2 : 1);
     const int R = p.R;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nt = (R + NB - 1) / NB;
     double* Zr = p.Z + (long long)r0 * R;
-    if ((nt - 1) % NW == warp) stage_block(p.Linv + (long long)(nt - 1) * NB * NB, ((nt - 1) & 1) ? lb1 : lb0, lane);
-    for (int J = nt - 1; J >= 0; --J) {
+    auto publish = [&](int J, const double* w) {
         const int j0 = J * NB, kb = min(NB, R - j0);
-        double (*x)[NB] = xs[J & 1];
-        if (J % NW == warp) {
-            cp_async_wait_all();
-            __syncwarp();
-            const double (*Ld)[NB + 1] = (J & 1) ? lb1 : lb0;
-            const double dinv = (lane < kb) ? Ld[lane][lane] : 0.0;
-            double w[NR];
+        if (lane < kb) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) w[r] = (lane < kb) ? __ldcg(Zr + (long long)r * R + j0 + lane) * dinv : 0.0;
-            for (int q = kb - 1; q > 0; --q) {
-                const double lq = (lane < q) ? Ld[q][lane] : 0.0;
-#pragma unroll
-                for (int r = 0; r < NR; ++r) w[r] = fma(-__shfl_sync(0xffffffffu, w[r], q), lq, w[r]);
-            }
-            if (lane < kb) {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    x[r][lane] = w[r];
-                    p.U[(long long)(r0 + r) * R + j0 + lane] = w[r];
-                }
+            for (int r = 0; r < NR; ++r) {
+                xs[J & 1][r][lane] = w[r];
+                p.U[(long long)(r0 + r) * R + j0 + lane] = w[r];
             }
         }
+    };
+    {   // the last block has nothing to its right
+        const int J = nt - 1, j0 = J * NB, kb = min(NB, R - j0);
+        if (warp == J % NW) {
+            stage_block(p.Linv + (long long)J * NB * NB, (J & 1) ? lb1 : lb0, lane);
+            cp_async_wait_all();
+            __syncwarp();
+            double w[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) w[r] = (lane < kb) ? __ldcg(Zr + (long long)r * R + j0 + lane) : 0.0;
+            back_diag<NR>((J & 1) ? lb1 : lb0, kb, lane, w);
+            publish(J, w);
+        }
+        if (J >= 1 && warp == (J - 1) % NW) stage_block(p.Linv + (long long)(J - 1) * NB * NB, ((J - 1) & 1) ? lb1 : lb0, lane);
         __syncthreads();
-        // the owner of the next block stages its diagonal block during this step
-        if (J > 0 && (J - 1) % NW == warp) stage_block(p.Linv + (long long)(J - 1) * NB * NB, ((J - 1) & 1) ? lb1 : lb0, lane);
+    }
+    for (int J = nt - 1; J >= 1; --J) {
+        const int j0 = J * NB, kb = min(NB, R - j0);
+        const double (*x)[NB] = xs[J & 1];
         const double* Ll = p.V + (long long)j0 * R + lane;     // L[j0 + q][lane + c] at q * R + c
-        // CB of the warp's column blocks per pass, so that a pass keeps 4 sums and
-        // CB loads per step of q in flight also when NR is small
-        constexpr int CB = (NR == 1) ? 4 : (NR == 2 ? 2 : 1);
-        int Jc = warp;
-        for (; Jc + NW * (CB - 1) < J; Jc += NW * CB) back_update<NR, CB>(Zr + lane, R, Ll, x, Jc * NB, kb);
-        for (; Jc < J; Jc += NW) back_update<NR, 1>(Zr + lane, R, Ll, x, Jc * NB, kb);
+        const int ow = (J - 1) % NW;
+        if (J >= 2 && warp == (J - 2) % NW) stage_block(p.Linv + (long long)(J - 2) * NB * NB, (J & 1) ? lb1 : lb0, lane);
+        if (warp == ow) {
+            double w[1][NR];
+            back_update<NR, 1, true>(Zr + lane, R, Ll, x, (J - 1) * NB, kb, 0, w);
+            cp_async_wait_all();
+            __syncwarp();
+            back_diag<NR>(((J - 1) & 1) ? lb1 : lb0, NB, lane, w[0]);
+            publish(J - 1, w[0]);
+        } else {
+            const int w7 = (warp - ow - 1 + NW) % NW;
+            int Jc = w7;
+            double acc[CB][NR];
+            for (; Jc + NO * (CB - 1) < J - 1; Jc += NO * CB) back_update<NR, CB>(Zr + lane, R, Ll, x, Jc * NB, kb, NO * NB, acc);
+            for (; Jc < J - 1; Jc += NO) back_update<NR, 1>(Zr + lane, R, Ll, x, Jc * NB, kb, NO * NB, acc);
+        }
+        __syncthreads();
     }
 }
 
