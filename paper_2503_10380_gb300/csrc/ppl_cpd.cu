@@ -168,7 +168,7 @@ bool plan(int o, int v, int X, int R, const ppl_cpd_opts& op, Layout& L) {
         L.Tt = take((size_t)R * v * L.ldk * e);            // per r: rows d, K = c
         L.W = take((size_t)rc * X * L.ldk * e);            // per r: rows Q, K = d
         L.Y = take((size_t)rc * X * L.ldk * e);            // rows r, K = (Q, c)
-        L.WTa = take((size_t)rc * v * kX * e);             // per r: rows c, K = Q
+        L.WTa = take((size_t)R * v * kX * e);              // per r: rows c, K = Q (every r: chain b fills it)
         L.WTb = take((size_t)rc * v * kX * e);
         L.S = take((size_t)rc * kvv * e);                  // rows r, K = (c, d)
         {
@@ -256,6 +256,11 @@ struct ppl_cpd {
         return opts.precision == PPL_PREC_TF32X3 ? 1 : 0;
     }
     bool dressed() const { return opts.dressed != 0; }
+    // bytes of one element of one operand plane
+    size_t plane_es() const { return opts.precision == PPL_PREC_BF16X3 ? 2 : 4; }
+    // the S-build takes W_a from the mode-b chain of the same sweep, unless the
+    // two are set to different accumulation restarts
+    bool reuse_wa() const { return ksub_p() == ksub(); }
 };
 
 namespace {
@@ -588,7 +593,7 @@ int t_tc(ppl_cpd* h) {
     // epilogue itself would be uncoalesced: consecutive rows d of a tile are a
     // panel row apart in Tt, and each 128-byte line of Tt takes one element
     // from each of 32 tiles; the transpose goes through shared memory instead.)
-    transpose_panels(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, v, bT, R, h->st);
+    transpose_panels(h->opts.precision, opb(h, h->L.T), opb(h, h->L.Tt), pT, pT, v, v, bT, bT, R, h->st);
     return PPL_OK;
 }
 
@@ -616,7 +621,9 @@ int run_tc_partial(ppl_cpd* h, TcGemm& g, double* out, long long ldo, const char
     return PPL_OK;
 }
 
-int chain_tc(ppl_cpd* h, int mode, double* Mout) {
+// keep_wa (mode b only): also store W = B U_a of every r-chunk, transposed per r
+// to rows c, K = Q, in L.WTa, where the S-build of the same sweep reads it
+int chain_tc(ppl_cpd* h, int mode, double* Mout, bool keep_wa) {
     const int v = h->v, X = h->X, R = h->R, rc = h->L.rc;
     const Pan q = pan_of(h);
     const long long pBn = (long long)X * v * q.ldk;       // Bn / Bp plane
@@ -637,6 +644,12 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
         g1.out = out_map(opb(h, h->L.W), pW, 0, v, plain(q.ke, q.ke), kpan((long long)X * q.ke), plain(bW, q.ke));
         int e = run_tc(h, g1, "W");
         if (e) return e;
+        if (keep_wa) {
+            // W[r][Q][c] (X rows per panel, K = c) -> WTa[r0 + r][c][Q] (v rows per panel, K = Q)
+            const long long bWT = (long long)v * q.kX;
+            transpose_panels(h->opts.precision, opb(h, h->L.W), opb(h, h->L.WTa + (size_t)r0 * bWT * h->plane_es()),
+                             pW, (long long)R * bWT, X, v, bW, bWT, rcur, h->st);
+        }
         // Y[r][Q][c] = sum_d T[r][c][d] W[r][Q][d]   (mode b: Tt, contracting c);
         // stored rows r, K (Q, c): m = c, n = Q, batch r
         TcGemm g2{};
@@ -660,37 +673,40 @@ int chain_tc(ppl_cpd* h, int mode, double* Mout) {
     return PPL_OK;
 }
 
-int p_tc_body(ppl_cpd* h);
-int p_tc(ppl_cpd* h) {
+int p_tc_body(ppl_cpd* h, bool wa_ready);
+int p_tc(ppl_cpd* h, bool wa_ready) {
     h->in_p = true;
-    const int e = p_tc_body(h);
+    const int e = p_tc_body(h, wa_ready);
     h->in_p = false;
     return e;
 }
-// W_a = B U_a and W_b = B U_b are both formed here per r-chunk.  (W_a is also
-// the W of the mode-b chain, but in the layout with c contiguous; the S
-// contraction needs Q contiguous, and writing that second layout from the
-// chain's epilogue would be uncoalesced, one 4-byte L2 request per element.)
-int p_tc_body(ppl_cpd* h) {
+// W_b = D-bar U_b is formed here per r-chunk.  W_a = B U_a is the W of the
+// mode-b chain: with wa_ready the chain of the same sweep (same U_a) has left
+// it in L.WTa, transposed to rows c, K = Q by a shared-memory transpose (a
+// second layout written by the chain's own epilogue would be uncoalesced, one
+// 4-byte L2 request per element); otherwise it is formed here too.
+int p_tc_body(ppl_cpd* h, bool wa_ready) {
     const int o = h->o, v = h->v, X = h->X, R = h->R, rc = h->L.rc;
     const Pan q = pan_of(h);
     const long long pBn = (long long)X * v * q.ldk;
     const long long pU = (long long)R * q.ldk;
     const long long bWT = (long long)v * q.kX;            // one r of WT
     const long long pWT = (long long)rc * bWT;            // one chunk of WT
+    const long long pWTa = (long long)R * bWT;            // WTa holds every r
     const long long pS = (long long)rc * q.kvv;
     double* P = h->at<double>(h->L.P);
     uop(h, 0, h->L.UopA);
     uop(h, 1, h->L.UopB);
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rcur = (R - r0 < rc) ? R - r0 : rc;
-        for (int w = 0; w < 2; ++w) {
+        for (int w = wa_ready ? 1 : 0; w < 2; ++w) {
             // WT[r] rows c, K Q: WT[r][c][Q] = sum_a B[Q][c][a] U[a][r0+r]; m = c*X + Q, n = r
             TcGemm g1{};
             g1.A = pmat(opb(h, (w == 1 && h->dressed()) ? h->L.BbT : h->L.BpW), pBn, v * X, v, 1, (long long)v * X, 0);
             g1.B = pmat(opb(h, w == 0 ? h->L.UopA : h->L.UopB), pU, R, v, 1, R, 0);
             g1.M = v * X; g1.N = rcur; g1.K = v; g1.batch = 1; g1.ksplit = 1; g1.b_row0 = r0; g1.nfast = 1;
-            g1.out = out_map(opb(h, w == 0 ? h->L.WTa : h->L.WTb), pWT, 0, X, plain(q.ke, q.ke),
+            g1.out = out_map(w == 0 ? opb(h, h->L.WTa + (size_t)r0 * bWT * h->plane_es()) : opb(h, h->L.WTb),
+                             w == 0 ? pWTa : pWT, 0, X, plain(q.ke, q.ke),
                              kpan((long long)v * q.ke), plain(bWT, q.ke));
             int e = run_tc(h, g1, "WT");
             if (e) return e;
@@ -698,7 +714,8 @@ int p_tc_body(ppl_cpd* h) {
         // S[r][c][d] = sum_Q WTa[r][c][Q] WTb[r][d][Q]; stored rows r, K (c, d): m = d, n = c, batch r
         TcGemm gs{};
         gs.A = pmat(opb(h, h->L.WTb), pWT, v, X, rc, v, bWT);
-        gs.B = pmat(opb(h, h->L.WTa), pWT, v, X, rc, v, bWT);
+        gs.B = pmat(opb(h, h->L.WTa), pWTa, v, X, R, v, bWT);
+        gs.b_b0 = r0;
         gs.a_bstep = 1; gs.b_bstep = 1;
         gs.M = v; gs.N = v; gs.K = X; gs.batch = rcur; gs.ksplit = 1;
         gs.out = out_map(opb(h, h->L.S), pS, q.ke, 0, Ix{0, 0}, kpan((long long)rc * q.ke), plain(q.ldk * rc, q.ke));
@@ -797,7 +814,7 @@ int prepare_operands(ppl_cpd* h, bool tau_only) {
     zero_bytes(opb(h, h->L.Tt), (size_t)h->R * v * q.ldk * eb, h->st);
     zero_bytes(opb(h, h->L.W), (size_t)h->L.rc * X * q.ldk * eb, h->st);
     zero_bytes(opb(h, h->L.Y), (size_t)h->L.rc * X * q.ldk * eb, h->st);
-    zero_bytes(opb(h, h->L.WTa), (size_t)h->L.rc * v * q.kX * eb, h->st);
+    zero_bytes(opb(h, h->L.WTa), (size_t)h->R * v * q.kX * eb, h->st);
     zero_bytes(opb(h, h->L.WTb), (size_t)h->L.rc * v * q.kX * eb, h->st);
     zero_bytes(opb(h, h->L.S), (size_t)h->L.rc * q.kvv * eb, h->st);
     zero_bytes(opb(h, h->L.Gop), (size_t)v * q.kvv * eb, h->st);
@@ -810,14 +827,14 @@ int mttkrp_into(ppl_cpd* h, int mode, double* Mout) {
         if (h->tc()) {
             int e = t_tc(h);
             if (e) return e;
-            return chain_tc(h, mode, Mout);
+            return chain_tc(h, mode, Mout, false);
         }
         t_fp64(h);
         mttkrp_ab_fp64(h, mode, Mout);
         return PPL_OK;
     }
     if (h->tc()) {
-        int e = p_tc(h);
+        int e = p_tc(h, false);
         if (e) return e;
     } else {
         p_fp64(h);
@@ -863,7 +880,7 @@ int sweep_phase(ppl_cpd* h, int q) {
         if (h->tc()) {
             if ((e = t_tc(h))) return e;
             mark(h, 1);
-            if ((e = chain_tc(h, 0, M))) return e;
+            if ((e = chain_tc(h, 0, M, false))) return e;
         } else {
             t_fp64(h);
             mark(h, 1);
@@ -874,7 +891,7 @@ int sweep_phase(ppl_cpd* h, int q) {
     case 1:
         mark(h, 3);
         if (h->tc()) {
-            if ((e = chain_tc(h, 1, M))) return e;
+            if ((e = chain_tc(h, 1, M, h->reuse_wa()))) return e;
         } else {
             mttkrp_ab_fp64(h, 1, M);
         }
@@ -883,7 +900,7 @@ int sweep_phase(ppl_cpd* h, int q) {
     case 2:
         mark(h, 5);
         if (h->tc()) {
-            if ((e = p_tc(h))) return e;
+            if ((e = p_tc(h, h->reuse_wa()))) return e;
         } else {
             p_fp64(h);
         }
@@ -1468,7 +1485,7 @@ int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out) {
         h->L.rc = c;
         for (int rep = 0; rep < 2 && !e; ++rep) {   // the first pass warms up
             cudaEventRecord(t0, h->st);
-            if (h->tc()) e = chain_tc(h, 0, M);
+            if (h->tc()) e = chain_tc(h, 0, M, false);
             else mttkrp_ab_fp64(h, 0, M);
             cudaEventRecord(t1, h->st);
         }

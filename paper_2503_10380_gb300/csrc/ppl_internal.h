@@ -155,10 +155,11 @@ void split_to_operand(int prec, const SplitSrc& s, int rows, int cols, int batch
 // c % kdiv < kmod when kdiv > 0) source element is written as zero.
 void split_to_panels(int prec, const SplitSrc& s, int rows, int prow, int cols, int kdiv, int kmod, int batch,
                      void* dst, long long plane_elems, cudaStream_t st);
-// Per-r transpose between K-panel layouts: src[b][d / KE][c][d % KE] = T_b[c][d]
-// (n x n, n rows per panel) to dst[b][c / KE][d][c % KE]; bstride elements per b.
-void transpose_panels(int prec, const void* src, void* dst, long long plane_elems, int n, long long bstride,
-                      int batch, cudaStream_t s);
+// Per-batch transpose between K-panel layouts: src[b][k / KE][a][k % KE] = X_b[a][k]
+// (A rows, B columns, A rows per panel) to dst[b][a / KE][k][a % KE] (B rows per
+// panel); plane_* elements from the hi to the lo plane, bstride_* elements per b.
+void transpose_panels(int prec, const void* src, void* dst, long long plane_s, long long plane_d, int A, int B,
+                      long long bstride_s, long long bstride_d, int batch, cudaStream_t s);
 // elements of one 128-byte operand row (the K-panel width) of a precision
 int panel_width(int prec);
 void zero_bytes(void* p, size_t n, cudaStream_t s);

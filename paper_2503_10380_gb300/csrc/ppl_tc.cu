@@ -783,31 +783,32 @@ __global__ void k_split_panels(SplitSrc s, int rows, int prow, int cols, int kdi
     }
 }
 
-// T_b[c][d] in [b][d / KE][c][d % KE] -> [b][c / KE][d][c % KE] (n rows per panel),
-// through a KE x KE tile in shared memory: both sides read and write whole
-// contiguous KE x KE blocks.
+// X_b[a][k] in [b][k / KE][a][k % KE] (A rows per panel, k < B) ->
+// [b][a / KE][k][a % KE] (B rows per panel), through a KE x KE tile in shared
+// memory: both sides read and write whole contiguous KE-element rows.
 template <typename T, int PLANES, int KE>
-__global__ void k_transpose_panels(const T* src, T* dst, long long plane, int n, long long bstride) {
+__global__ void k_transpose_panels(const T* src, T* dst, long long plane_s, long long plane_d, int A, int B,
+                                   long long bstride_s, long long bstride_d) {
     __shared__ T tile[PLANES][KE][KE + 1];
     const int b = blockIdx.z;
-    const int c0 = blockIdx.y * KE, d0 = blockIdx.x * KE;    // this block: c in [c0, c0+KE), d in [d0, d0+KE)
-    if (c0 >= n || d0 >= n) return;
-    const long long off = (long long)b * bstride;
-    const long long pan = (long long)n * KE;
+    const int a0 = blockIdx.y * KE, k0 = blockIdx.x * KE;    // this block: a in [a0, a0+KE), k in [k0, k0+KE)
+    if (a0 >= A || k0 >= B) return;
+    const long long os = (long long)b * bstride_s, od = (long long)b * bstride_d;
+    const long long pan_s = (long long)A * KE, pan_d = (long long)B * KE;
     for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
-        const int ci = e / KE, di = e % KE;          // reads: d fastest
-        const int c = c0 + ci, d = d0 + di;
+        const int ai = e / KE, ki = e % KE;          // reads: k fastest
+        const int a = a0 + ai, k = k0 + ki;
         for (int pl = 0; pl < PLANES; ++pl)
-            tile[pl][ci][di] = (c < n && d < n) ? src[pl * plane + off + (long long)(d / KE) * pan + (long long)c * KE + d % KE]
+            tile[pl][ai][ki] = (a < A && k < B) ? src[pl * plane_s + os + (long long)(k / KE) * pan_s + (long long)a * KE + k % KE]
                                                 : T(0);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
-        const int di = e / KE, ci = e % KE;          // writes: c fastest
-        const int c = c0 + ci, d = d0 + di;
-        if (c < n && d < n)
+        const int ki = e / KE, ai = e % KE;          // writes: a fastest
+        const int a = a0 + ai, k = k0 + ki;
+        if (a < A && k < B)
             for (int pl = 0; pl < PLANES; ++pl)
-                dst[pl * plane + off + (long long)(c / KE) * pan + (long long)d * KE + c % KE] = tile[pl][ci][di];
+                dst[pl * plane_d + od + (long long)(a / KE) * pan_d + (long long)k * KE + a % KE] = tile[pl][ai][ki];
     }
 }
 
@@ -1032,21 +1033,18 @@ void split_to_panels(int prec, const SplitSrc& s, int rows, int prow, int cols, 
                                                                             batch, dst, plane_elems);
 }
 
-void transpose_panels(int prec, const void* src, void* dst, long long plane_elems, int n, long long bstride,
-                      int batch, cudaStream_t s) {
-    if (n <= 0 || batch <= 0) return;
+void transpose_panels(int prec, const void* src, void* dst, long long plane_s, long long plane_d, int A, int B,
+                      long long bstride_s, long long bstride_d, int batch, cudaStream_t s) {
+    if (A <= 0 || B <= 0 || batch <= 0) return;
     if (prec == PPL_PREC_BF16X3) {
-        const int t = (n + 63) / 64;
-        k_transpose_panels<unsigned short, 2, 64><<<dim3(t, t, batch), 256, 0, s>>>(
-            (const unsigned short*)src, (unsigned short*)dst, plane_elems, n, bstride);
+        k_transpose_panels<unsigned short, 2, 64><<<dim3((B + 63) / 64, (A + 63) / 64, batch), 256, 0, s>>>(
+            (const unsigned short*)src, (unsigned short*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
+    } else if (prec == PPL_PREC_TF32X3) {
+        k_transpose_panels<float, 2, 32><<<dim3((B + 31) / 32, (A + 31) / 32, batch), 256, 0, s>>>(
+            (const float*)src, (float*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
     } else {
-        const int t = (n + 31) / 32;
-        if (prec == PPL_PREC_TF32X3)
-            k_transpose_panels<float, 2, 32><<<dim3(t, t, batch), 256, 0, s>>>((const float*)src, (float*)dst,
-                                                                               plane_elems, n, bstride);
-        else
-            k_transpose_panels<float, 1, 32><<<dim3(t, t, batch), 256, 0, s>>>((const float*)src, (float*)dst,
-                                                                               plane_elems, n, bstride);
+        k_transpose_panels<float, 1, 32><<<dim3((B + 31) / 32, (A + 31) / 32, batch), 256, 0, s>>>(
+            (const float*)src, (float*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
     }
 }
 

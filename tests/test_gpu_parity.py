@@ -205,6 +205,30 @@ def test_mixed_sweeps_track_fp64_energy(prec, kcal_tol, ftol):
     cp.close()
 
 
+@pytest.mark.parametrize("prec,ftol", [("tf32x3", 2e-4), ("bf16x3", 2e-2)])
+@pytest.mark.parametrize("acc_steps_p", [0, 1])
+@pytest.mark.parametrize("dressed", [False, True])
+def test_sweeps_over_several_r_chunks(prec, ftol, acc_steps_p, dressed):
+    """Config 0 in r-chunks of 16 rank columns (three passes of every chain
+    and of the S-build), 10 sweeps against oracle ALS from the same start.
+    With acc_steps_p = 0 the S-build reads W_a = B U_a from the mode-b chain of
+    the same sweep, transposed per r-chunk into a buffer over all R columns;
+    with acc_steps_p = 1 (a different accumulator restart from the chain's) it
+    forms W_a itself.  Dressed: D-bar on the b side of every contraction
+    (Eq. fulldfB), so the S-build's W_b has another operand than W_a."""
+    inp = inputs.make_inputs(5, 24, 72, 48, seed=0)
+    Bbar = orc.dress(inp.B, inp.t1, 5) if dressed else None
+    U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 10, 1.0, Bbar=Bbar)
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), inp.factors, precision=prec, r_chunk=16,
+                       acc_steps_p=acc_steps_p, dressed=dressed)
+    if dressed:
+        cp.set_t1(_dev(inp.t1))
+    cp.sweep(10)
+    _check_factors(_factors(cp), U_ref, lam_ref, ftol,
+                   f"{prec} r-chunks of 16, acc_steps_p={acc_steps_p}, dressed={dressed}")
+    cp.close()
+
+
 def test_graph_replay_equals_direct_launches():
     inp = inputs.make_inputs(4, 20, 30, 40, seed=5)
     U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 3)
