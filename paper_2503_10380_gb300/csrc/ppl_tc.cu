@@ -812,6 +812,60 @@ __global__ void k_transpose_panels(const T* src, T* dst, long long plane_s, long
     }
 }
 
+// The same for 4-byte elements (KE = 32) with 16-byte accesses: thread t reads
+// row a0 + t / 8, elements 4 (t % 8) .. + 3 of a tile's 128-byte source row and
+// writes row k0 + t / 8, elements 4 (t % 8) .. + 3 of a destination row; the
+// padded shared tile makes both sides conflict-free.  vec = 0 (offsets that are
+// not multiples of 4 elements) and the ragged edge tiles go element by element.
+template <int PLANES>
+__global__ void __launch_bounds__(256) k_transpose_panels4(const float* src, float* dst, long long plane_s,
+                                                           long long plane_d, int A, int B, long long bstride_s,
+                                                           long long bstride_d, int vec) {
+    constexpr int KE = 32;
+    __shared__ float tile[PLANES][KE][KE + 1];
+    const int b = blockIdx.z;
+    const int a0 = blockIdx.y * KE, k0 = blockIdx.x * KE;
+    if (a0 >= A || k0 >= B) return;
+    const long long os = (long long)b * bstride_s, od = (long long)b * bstride_d;
+    const long long pan_s = (long long)A * KE, pan_d = (long long)B * KE;
+    if (vec && a0 + KE <= A && k0 + KE <= B) {
+        const int r = threadIdx.x >> 3, q = (threadIdx.x & 7) * 4;
+        const float* sp = src + os + (long long)blockIdx.x * pan_s + (long long)(a0 + r) * KE + q;
+        float4 v[PLANES];
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl) v[pl] = *(const float4*)(sp + pl * plane_s);
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl) {
+            tile[pl][r][q] = v[pl].x;
+            tile[pl][r][q + 1] = v[pl].y;
+            tile[pl][r][q + 2] = v[pl].z;
+            tile[pl][r][q + 3] = v[pl].w;
+        }
+        __syncthreads();
+        float* dp = dst + od + (long long)blockIdx.y * pan_d + (long long)(k0 + r) * KE + q;
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl)
+            *(float4*)(dp + pl * plane_d) =
+                make_float4(tile[pl][q][r], tile[pl][q + 1][r], tile[pl][q + 2][r], tile[pl][q + 3][r]);
+        return;
+    }
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int ai = e / KE, ki = e % KE;
+        const int a = a0 + ai, k = k0 + ki;
+        for (int pl = 0; pl < PLANES; ++pl)
+            tile[pl][ai][ki] = (a < A && k < B) ? src[pl * plane_s + os + (long long)blockIdx.x * pan_s + (long long)a * KE + ki]
+                                                : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int ki = e / KE, ai = e % KE;
+        const int a = a0 + ai, k = k0 + ki;
+        if (a < A && k < B)
+            for (int pl = 0; pl < PLANES; ++pl)
+                dst[pl * plane_d + od + (long long)blockIdx.y * pan_d + (long long)k * KE + ai] = tile[pl][ai][ki];
+    }
+}
+
 bool make_map(CUtensorMap* m, int prec, const void* ptr, const TcMat& t, int box_rows) {
     const bool split = (prec == PPL_PREC_BF16X3);   // 2-byte elements
     const size_t es = split ? 2 : 4;
@@ -1039,12 +1093,17 @@ void transpose_panels(int prec, const void* src, void* dst, long long plane_s, l
     if (prec == PPL_PREC_BF16X3) {
         k_transpose_panels<unsigned short, 2, 64><<<dim3((B + 63) / 64, (A + 63) / 64, batch), 256, 0, s>>>(
             (const unsigned short*)src, (unsigned short*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
-    } else if (prec == PPL_PREC_TF32X3) {
-        k_transpose_panels<float, 2, 32><<<dim3((B + 31) / 32, (A + 31) / 32, batch), 256, 0, s>>>(
-            (const float*)src, (float*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
     } else {
-        k_transpose_panels<float, 1, 32><<<dim3((B + 31) / 32, (A + 31) / 32, batch), 256, 0, s>>>(
-            (const float*)src, (float*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
+        auto m4 = [](long long x) { return x % 4 == 0; };
+        const int vec = m4(plane_s) && m4(plane_d) && m4(bstride_s) && m4(bstride_d) &&
+                        (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0;
+        const dim3 grid((B + 31) / 32, (A + 31) / 32, batch);
+        if (prec == PPL_PREC_TF32X3)
+            k_transpose_panels4<2><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, plane_s, plane_d, A, B,
+                                                       bstride_s, bstride_d, vec);
+        else
+            k_transpose_panels4<1><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, plane_s, plane_d, A, B,
+                                                       bstride_s, bstride_d, vec);
     }
 }
 
