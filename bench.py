@@ -368,19 +368,25 @@ MTTKRP_PHASES = ("tau_r", "chain_a", "chain_b", "s_and_p")
 SOLVE_PHASES = ("solve_a", "solve_b", "solve_ij")
 
 
-def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None):
+def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None, mttkrp_modes="abij"):
     """k sweeps from the same start in `precision` and in the plain FP64 GPU form:
     energy difference (kcal/mol and relative), per-factor errors, and the FP64
-    form's time per sweep (its first sweep captures the graph and is not timed)."""
+    form's time per sweep (its first sweep captures the graph and is not timed).
+    Before the sweeps, the MTTKRP of each mode in `mttkrp_modes` from the common
+    starting factors in both forms: modes a and b run T, W, Y and M (the chain),
+    modes i and j the S-build (W_a, W_b, S, P), so their errors locate where the
+    split precision loses accuracy."""
     import torch
     from paper_2503_10380_gb300 import binding
     mixed = binding.CpAls(B, tau, fac, precision=precision, r_chunk=r_chunk)
+    M_mixed = {m: mixed.mttkrp(m).cpu().numpy() for m in mttkrp_modes}
     mixed.sweep(k, want_hist=False)
     E_mixed, F_mixed = mixed.energy(), _factors_host(mixed)
     mixed.close()
     del mixed
     torch.cuda.empty_cache()
     f64 = binding.CpAls(B, tau, fac, precision="fp64")
+    M64 = {m: f64.mttkrp(m).cpu().numpy() for m in mttkrp_modes}
     f64.sweep(1, want_hist=False)
     f64_ms = _time_sweeps(f64, k - 1, stream) if k > 1 else None
     E64, F64 = f64.energy(), _factors_host(f64)
@@ -390,7 +396,8 @@ def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None):
     d = abs(E_mixed - E64)
     out = {"sweeps": k, "E_cp_mixed": E_mixed, "E_cp_fp64": E64, "dE_kcal_per_mol": d * KCAL,
            "dE_rel": d / abs(E64), "meets_0.1_kcal": d * KCAL <= 0.1,
-           "factor_rel_err": factor_errors(F_mixed, F64), "fp64_ms_per_sweep": f64_ms}
+           "factor_rel_err": factor_errors(F_mixed, F64), "fp64_ms_per_sweep": f64_ms,
+           "mttkrp_rel_err_at_start": factor_errors(M_mixed, M64)}
     if E_exact is not None:
         out["E_exact"] = E_exact
         out["rank_error_kcal_per_mol"] = abs(E64 - E_exact) * KCAL
@@ -517,7 +524,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
 
     # ---- accuracy against the plain FP64 GPU form from the same start ---------
-    acc = accuracy_vs_fp64(B, tau, fac, args.precision, args.r_chunk, ACC_SWEEPS_MAIN, stream, E_exact)
+    acc = accuracy_vs_fp64(B, tau, fac, args.precision, args.r_chunk, ACC_SWEEPS_MAIN, stream, E_exact,
+                           mttkrp_modes="ai")
     del B, tau
     torch.cuda.empty_cache()
 
