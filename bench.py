@@ -368,27 +368,36 @@ MTTKRP_PHASES = ("tau_r", "chain_a", "chain_b", "s_and_p")
 SOLVE_PHASES = ("solve_a", "solve_b", "solve_ij")
 
 
-def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None, mttkrp_modes="abij"):
+def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None, mttkrp_modes="abij", normR2=None):
     """k sweeps from the same start in `precision` and in the plain FP64 GPU form:
     energy difference (kcal/mol and relative), per-factor errors, and the FP64
     form's time per sweep (its first sweep captures the graph and is not timed).
     Before the sweeps, the MTTKRP of each mode in `mttkrp_modes` from the common
     starting factors in both forms: modes a and b run T, W, Y and M (the chain),
     modes i and j the S-build (W_a, W_b, S, P), so their errors locate where the
-    split precision loses accuracy."""
+    split precision loses accuracy.  With normR2 (||R||^2), also the fit of both
+    forms after the k sweeps (Eq. cpfit through the residual expansion): their
+    difference is the noise floor a |delta fit| stopping test meets in the split
+    precision."""
     import torch
     from paper_2503_10380_gb300 import binding
     mixed = binding.CpAls(B, tau, fac, precision=precision, r_chunk=r_chunk)
     M_mixed = {m: mixed.mttkrp(m).cpu().numpy() for m in mttkrp_modes}
+    if normR2 is not None:
+        mixed.set_normR2(normR2)
     mixed.sweep(k, want_hist=False)
+    fit_mixed = mixed.fit() if normR2 is not None else None
     E_mixed, F_mixed = mixed.energy(), _factors_host(mixed)
     mixed.close()
     del mixed
     torch.cuda.empty_cache()
     f64 = binding.CpAls(B, tau, fac, precision="fp64")
     M64 = {m: f64.mttkrp(m).cpu().numpy() for m in mttkrp_modes}
+    if normR2 is not None:
+        f64.set_normR2(normR2)
     f64.sweep(1, want_hist=False)
     f64_ms = _time_sweeps(f64, k - 1, stream) if k > 1 else None
+    fit64 = f64.fit() if normR2 is not None else None
     E64, F64 = f64.energy(), _factors_host(f64)
     f64.close()
     del f64
@@ -398,6 +407,9 @@ def accuracy_vs_fp64(B, tau, fac, precision, r_chunk, k, stream, E_exact=None, m
            "dE_rel": d / abs(E64), "meets_0.1_kcal": d * KCAL <= 0.1,
            "factor_rel_err": factor_errors(F_mixed, F64), "fp64_ms_per_sweep": f64_ms,
            "mttkrp_rel_err_at_start": factor_errors(M_mixed, M64)}
+    if normR2 is not None:
+        out["fit_mixed"], out["fit_fp64"] = fit_mixed, fit64
+        out["fit_abs_diff"] = abs(fit_mixed - fit64)
     if E_exact is not None:
         out["E_exact"] = E_exact
         out["rank_error_kcal_per_mol"] = abs(E64 - E_exact) * KCAL
@@ -517,7 +529,7 @@ def run_ours(args, world, rank, local):
     del tau_h
     # ||R||^2 and E_exact once, from the tensor-core exact contraction
     t0 = time.perf_counter()
-    _, E_exact, _ = cp.exact_contract(mixed=True)
+    normR2, E_exact, _ = cp.exact_contract(mixed=True)
     t_exact = time.perf_counter() - t0
     cp.close()
     del cp
@@ -525,7 +537,7 @@ def run_ours(args, world, rank, local):
 
     # ---- accuracy against the plain FP64 GPU form from the same start ---------
     acc = accuracy_vs_fp64(B, tau, fac, args.precision, args.r_chunk, ACC_SWEEPS_MAIN, stream, E_exact,
-                           mttkrp_modes="ai")
+                           mttkrp_modes="ai", normR2=normR2)
     del B, tau
     torch.cuda.empty_cache()
 

@@ -19,6 +19,9 @@
 #include <new>
 #include <string>
 #include <algorithm>
+#include <map>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/ppl_cpd.h"
@@ -55,6 +58,9 @@ constexpr int RC_MAX = 1024; // most rank columns per pass of the chain
 #endif
 #ifndef BATCH_TC_SHARE
 #define BATCH_TC_SHARE 4        // a batched tensor-core contraction takes about SHARE / nstreams of the SMs (0: all)
+#endif
+#ifndef BATCH_GROUP_SETS
+#define BATCH_GROUP_SETS 4      // grouped contraction launches per depth of a batch graph
 #endif
 #ifndef BATCH_SOLVE_SHARE
 #define BATCH_SOLVE_SHARE 4     // a batched solve takes about SHARE / nstreams of the SMs
@@ -1552,6 +1558,116 @@ int ppl_cpd_inject_wait_timeout(ppl_cpd* h) {
 
 }  // extern "C"
 
+namespace {
+
+// Merge the tensor-core contractions of a captured batch graph into grouped
+// launches.  Every instance's work is a chain of nodes; a contraction's depth is
+// the number of contractions on the longest path that ends in it.  Contractions
+// of equal depth (and kernel) lie on no common path, so each such set becomes one
+// persistent launch (at most tc_group_capacity() contractions each) that depends
+// on all of the members' predecessors and precedes all of their successors.
+// Returns 0, or a CUDA error code; *removed counts the launches saved.
+int group_contractions(cudaGraph_t g, long long* removed) {
+    *removed = 0;
+    size_t nn = 0, ne = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return -1;
+    if (cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> from(ne), to(ne);
+    if (ne && cudaGraphGetEdges(g, from.data(), to.data(), nullptr, &ne) != cudaSuccess) return -1;
+    std::unordered_map<cudaGraphNode_t, int> id;
+    for (size_t i = 0; i < nn; ++i) id[nodes[i]] = (int)i;
+    std::vector<std::vector<int>> succ(nn), pred(nn);
+    for (size_t e = 0; e < ne; ++e) {
+        succ[id[from[e]]].push_back(id[to[e]]);
+        pred[id[to[e]]].push_back(id[from[e]]);
+    }
+    std::vector<const void*> func(nn, nullptr), arg0(nn, nullptr);
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) return -1;
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nodes[i], &kp) != cudaSuccess) return -1;
+        if (tc_group_kernel(kp.func) && kp.kernelParams) {
+            func[i] = kp.func;
+            arg0[i] = kp.kernelParams[0];
+        }
+    }
+    // depths in topological order
+    std::vector<int> indeg(nn), depth(nn, 0), order;
+    order.reserve(nn);
+    for (size_t i = 0; i < nn; ++i) {
+        indeg[i] = (int)pred[i].size();
+        if (!indeg[i]) order.push_back((int)i);
+    }
+    for (size_t q = 0; q < order.size(); ++q) {
+        const int v = order[q];
+        if (func[v]) depth[v] += 1;
+        for (int w : succ[v]) {
+            depth[w] = std::max(depth[w], depth[v]);
+            if (--indeg[w] == 0) order.push_back(w);
+        }
+    }
+    if (order.size() != nn) return -2;   // not a DAG: leave the graph as it is
+    std::map<std::pair<int, const void*>, std::vector<int>> sets;
+    for (size_t i = 0; i < nn; ++i)
+        if (func[i]) sets[{depth[i], func[i]}].push_back((int)i);
+    const int cap = tc_group_capacity();
+    // replaced node -> its group node (sets are visited by increasing depth, so a
+    // member's predecessors may be contractions replaced earlier)
+    std::unordered_map<cudaGraphNode_t, cudaGraphNode_t> repl;
+    for (auto& kv : sets) {
+        const std::vector<int>& all = kv.second;
+        if (all.size() < 2) continue;
+        // a few groups per depth rather than one: each holds a run of instances in
+        // capture order, so the groups' chains stay largely independent and the
+        // small kernels of one overlap the contractions of another
+        int nparts = (int)((all.size() + cap - 1) / cap);
+        const int sets = std::min<int>(BATCH_GROUP_SETS, (int)all.size() / 2);
+        if (nparts < sets) nparts = sets;
+        for (int part = 0; part < nparts; ++part) {
+            const size_t b0 = all.size() * part / nparts, b1 = all.size() * (part + 1) / nparts;
+            if (b1 - b0 < 2) continue;
+            std::vector<const void*> args;
+            std::vector<cudaGraphNode_t> deps, outs;
+            for (size_t k = b0; k < b1; ++k) {
+                const int m = all[k];
+                args.push_back(arg0[m]);
+                for (int u : pred[m]) {
+                    cudaGraphNode_t d = nodes[u];
+                    const auto r = repl.find(d);
+                    if (r != repl.end()) d = r->second;
+                    if (std::find(deps.begin(), deps.end(), d) == deps.end()) deps.push_back(d);
+                }
+                for (int w : succ[m])
+                    if (std::find(outs.begin(), outs.end(), nodes[w]) == outs.end()) outs.push_back(nodes[w]);
+            }
+            cudaKernelNodeParams kp{};
+            void* storage = nullptr;
+            if (tc_group_node_params(kv.first.second, args.data(), (int)args.size(), &kp, &storage) != 0) continue;
+            cudaGraphNode_t gn;
+            cudaError_t ce = cudaGraphAddKernelNode(&gn, g, deps.data(), deps.size(), &kp);
+            tc_group_release(storage);
+            if (ce != cudaSuccess) return (int)ce;
+            for (cudaGraphNode_t w : outs) {
+                ce = cudaGraphAddDependencies(g, &gn, &w, nullptr, 1);
+                if (ce != cudaSuccess) return (int)ce;
+            }
+            for (size_t k = b0; k < b1; ++k) {
+                ce = cudaGraphDestroyNode(nodes[all[k]]);
+                if (ce != cudaSuccess) return (int)ce;
+                repl[nodes[all[k]]] = gn;
+            }
+            *removed += (long long)(b1 - b0) - 1;
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
 struct ppl_cpd_batch {
     std::vector<ppl_cpd*> hs;
     std::vector<cudaStream_t> streams;
@@ -1595,7 +1711,9 @@ int ppl_cpd_batch_create(ppl_cpd_batch** bp, int n, ppl_cpd* const* handles, int
             handles[k]->tc_cap = tcap;
         }
     }
-    for (int i = 0; ok && i < ns; ++i) {
+    // one capture stream per instance: every instance's work is its own chain in the
+    // graph, so that contractions of equal depth can be grouped (group_contractions)
+    for (int i = 0; ok && i < n; ++i) {
         cudaStream_t s;
         cudaEvent_t e;
         ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1666,6 +1784,13 @@ int ppl_cpd_batch_sweep(ppl_cpd_batch* b, int nsweeps, double* fits) {
             return err;
         }
         if (ce != cudaSuccess) return fail(nullptr, PPL_ECUDA, "batch end capture: %s", cudaGetErrorString(ce));
+        long long saved = 0;
+        const int ge = group_contractions(gr, &saved);
+        if (ge != 0) {
+            cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return fail(nullptr, PPL_ECUDA, "batch: grouping the contractions failed (%d)", ge);
+        }
         ce = cudaGraphInstantiate(&b->exec, gr, 0);
         if (ce != cudaSuccess) {
             cudaGraphDestroy(gr);

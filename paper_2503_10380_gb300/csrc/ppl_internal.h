@@ -142,6 +142,17 @@ void reduce_partials(const float* part, int ksplit, int M, int N, double* out, l
 void transpose_operand(int prec, const void* src, void* dst, long long plane_elems, int n, long long ld,
                        long long bstride, int batch, cudaStream_t s);
 int tc_init_driver();   // resolves cuTensorMapEncodeTiled; returns 0 on success
+// Several independent contractions in one persistent launch.  A captured launch
+// of tc_gemm is a kernel node whose kernelParams[0] is its argument block; the
+// grouped kernel walks the tiles of up to tc_group_capacity() such contractions.
+// tc_group_kernel: the grouped counterpart of a single-contraction kernel (nullptr
+// if f is not one).  tc_group_node_params: the kernel-node parameters of one
+// grouped launch of the n argument blocks args (all of kernel f); *storage holds
+// them until tc_group_release, after the node is created.  Returns 0 on success.
+const void* tc_group_kernel(const void* f);
+int tc_group_capacity();
+int tc_group_node_params(const void* f, const void* const* args, int n, cudaKernelNodeParams* out, void** storage);
+void tc_group_release(void* storage);
 // FP64 -> operand planes: dst[b][r][c] from src with generic index maps, rows x cols per batch
 struct SplitSrc {
     const double* src; Idx2 rmap, cmap; long long bstride;

@@ -32,6 +32,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include "../../include/ppl_cpd.h"
 
@@ -80,6 +81,25 @@ struct KParams {
     unsigned long long wait_ns;   // bound of every barrier wait
     unsigned int* err;
 };
+
+// One contraction: the tensor maps of A hi, A lo, B hi, B lo and its parameters.
+struct TcArgs {
+    CUtensorMap m[4];
+    KParams p;
+};
+// Several independent contractions in one persistent launch (one CUDA graph
+// node): the CTAs walk the concatenated tile lists; tile0[i] is the first tile
+// of contraction i.  The shared-memory stages and the TMEM accumulators are laid
+// out for the widest N tile of the group.
+constexpr int TC_GROUP_MAX = 40;
+struct TcGroupArgs {
+    int n, bn_max, stages, acc_cols;
+    unsigned long long wait_ns;
+    int tile0[TC_GROUP_MAX + 1];
+    CUtensorMap m[TC_GROUP_MAX][4];
+    KParams p[TC_GROUP_MAX];
+};
+static_assert(sizeof(TcGroupArgs) <= 32000, "kernel parameter space");
 
 // operand traits of the precisions
 template <int PREC> struct Prec {
@@ -319,20 +339,33 @@ __device__ __forceinline__ void emit32(const KParams& p, long long mo, int n0, i
     }
 }
 
+// tiles of one contraction
+__host__ __device__ __forceinline__ int tc_tiles(const KParams& p) {
+    return ((p.M + TM - 1) / TM) * ((p.N + p.bn - 1) / p.bn) * p.batch * p.ksplit;
+}
+
+// The kernel body for nprob contractions: P[i] and the four maps M4[4 i .. 4 i + 3]
+// of contraction i, whose tiles are tile0[i] .. tile0[i + 1] - 1 of the walk
+// (tile0 == nullptr: one contraction).  Stages of bn_max-wide B tiles, S of them,
+// and two TMEM accumulators of acc_cols_u columns serve every contraction.
 template <int PREC, bool DRAIN>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const KParams p) {
+__device__ __forceinline__ void tc_body(const KParams* P, const CUtensorMap* M4, const int* tile0, int nprob,
+                                        int bn_max, int S, int acc_cols_u, unsigned long long wait_ns) {
     constexpr bool SPLIT = (Prec<PREC>::PLANES == 2);
     constexpr int KE = Prec<PREC>::KE;
     constexpr int KSTEP = Prec<PREC>::KSTEP;
     constexpr int ASTEP_BYTES = 32;           // one MMA's K slice of a 128-byte row
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn;
-    const int tiles_mn = ntm * ntn;
-    const int total = tiles_mn * p.batch * p.ksplit;
-    const int S = p.stages;
+    const int total = tile0 ? tile0[nprob] : tc_tiles(P[0]);
+    // contraction of walk tile t and the tile's index inside it
+    auto locate = [&](int t, int& lt) -> int {
+        int pi = 0;
+        if (tile0)
+            while (pi + 1 < nprob && tile0[pi + 1] <= t) ++pi;
+        lt = tile0 ? t - tile0[pi] : t;
+        return pi;
+    };
 
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -340,7 +373,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     unsigned char* gbase = smem_raw + (base - raw);
 
     const uint32_t a_bytes = TM * KROW_BYTES;
-    const uint32_t b_bytes = (uint32_t)p.bn * KROW_BYTES;
+    const uint32_t b_bytes = (uint32_t)bn_max * KROW_BYTES;          // stage layout: the widest B tile
     const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (a_bytes + b_bytes);
     const uint32_t bar_off = stage_bytes * S;
     const uint32_t full0 = base + bar_off;
@@ -353,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ int s_fail;
     __shared__ int s_issued, s_consumed;
 
-    const uint32_t acc_cols = (uint32_t)p.acc_cols;
+    const uint32_t acc_cols = (uint32_t)acc_cols_u;
     const uint32_t ncols = 2u * acc_cols;
 
     if (threadIdx.x == 0) {
@@ -371,8 +404,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mAh) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mBh) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&M4[0]) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&M4[2]) : "memory");
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
@@ -393,7 +426,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // TMA producer: one ring of S stages shared by all tiles of this block
                 int it = 0;
                 for (int t = blockIdx.x; t < total && !*vfail; t += gridDim.x) {
-                    const int z = t / tiles_mn, rem = t % tiles_mn;
+                    int lt;
+                    const int pi = locate(t, lt);
+                    const KParams& p = P[pi];
+                    const CUtensorMap* mp = M4 + 4 * pi;
+                    const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn, tiles_mn = ntm * ntn;
+                    const uint32_t tx_bytes = (SPLIT ? 2u : 1u) * (a_bytes + (uint32_t)p.bn * KROW_BYTES);
+                    const int z = lt / tiles_mn, rem = lt % tiles_mn;
                     const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
                     const int bz = z / p.ksplit, ks = z % p.ksplit;
                     const int kb0 = ks * p.per_split;
@@ -401,20 +440,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int a_b = p.a_b0 + bz * p.a_bstep, b_b = p.b_b0 + bz * p.b_bstep;
                     for (int kbi = 0; kbi < nk; ++kbi, ++it) {
                         const int s = it % S;
-                        if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1), p.wait_ns)) {
+                        if (it >= S && !mbar_wait(empty0 + 8u * s, (uint32_t)((it / S - 1) & 1), wait_ns)) {
                             atomicOr(p.err, 1u);
                             *vfail = 1;
                             break;
                         }
                         const uint32_t sa = base + stage_bytes * s;
                         const uint32_t fb = full0 + 8u * s;
-                        mbar_expect_tx(fb, stage_bytes);
+                        mbar_expect_tx(fb, tx_bytes);
                         const int kb = kb0 + kbi;
-                        load_op(sa, &mAh, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
-                        load_op(sa + (SPLIT ? 2u : 1u) * a_bytes, &mBh, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
+                        load_op(sa, &mp[0], p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                        load_op(sa + (SPLIT ? 2u : 1u) * a_bytes, &mp[2], p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
                         if constexpr (SPLIT) {
-                            load_op(sa + a_bytes, &mAl, p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
-                            load_op(sa + 2u * a_bytes + b_bytes, &mBl, p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
+                            load_op(sa + a_bytes, &mp[1], p.a_panel, kb, KE, p.a_row0 + m0, a_b, fb);
+                            load_op(sa + 2u * a_bytes + b_bytes, &mp[3], p.b_panel, kb, KE, p.b_row0 + n0, b_b, fb);
                         }
                         s_issued = it + 1;
                     }
@@ -423,12 +462,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         } else if (warp == 1) {
             if (lane == 0) {
                 // MMA issuer
-                uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
-                idesc |= Prec<PREC>::HALF ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
                 int it = 0, li = 0;   // li counts accumulation chunks (one per tile unless DRAIN)
                 bool ok = true;
                 for (int t = blockIdx.x; t < total && ok && !*vfail; t += gridDim.x) {
-                    const int z = t / tiles_mn;
+                    int lt;
+                    const KParams& p = P[locate(t, lt)];
+                    uint32_t idesc = (1u << 4) | ((uint32_t)p.bn >> 3 << 17) | ((uint32_t)(TM >> 4) << 24);
+                    idesc |= Prec<PREC>::HALF ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+                    const int tiles_mn = ((p.M + TM - 1) / TM) * ((p.N + p.bn - 1) / p.bn);
+                    const int z = lt / tiles_mn;
                     const int ks = z % p.ksplit;
                     const int kb0 = ks * p.per_split;
                     const int nk = min(p.per_split, p.nkb_total - kb0);
@@ -437,7 +479,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         // each K block in chunks of ksub MMA K steps, one accumulator each
                         for (int kbi = 0; kbi < nk && ok; ++kbi, ++it) {
                             const int s = it % S;
-                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
+                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), wait_ns)) {
                                 atomicOr(p.err, 2u);
                                 *vfail = 1;
                                 ok = false;
@@ -455,7 +497,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             for (int kk0 = 0; kk0 < ksteps; kk0 += p.ksub, ++li) {
                                 const int kk1 = min(ksteps, kk0 + p.ksub);
                                 const int buf = li & 1;
-                                if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
+                                if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), wait_ns)) {
                                     atomicOr(p.err, 8u);
                                     *vfail = 1;
                                     ok = false;
@@ -490,7 +532,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int kc0 = 0; kc0 < nk && ok; kc0 += kch, ++li) {
                         const int kc1 = min(nk, kc0 + kch);
                         const int buf = li & 1;
-                        if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), p.wait_ns)) {
+                        if (li >= 2 && !mbar_wait(tempty0 + 8u * buf, (uint32_t)(((li >> 1) - 1) & 1), wait_ns)) {
                             atomicOr(p.err, 8u);
                             *vfail = 1;
                             ok = false;
@@ -500,7 +542,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint32_t d = tmem + (uint32_t)buf * acc_cols;
                         for (int kbi = kc0; kbi < kc1; ++kbi, ++it) {
                             const int s = it % S;
-                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), p.wait_ns)) {
+                            if (!mbar_wait(full0 + 8u * s, (uint32_t)((it / S) & 1), wait_ns)) {
                                 atomicOr(p.err, 2u);
                                 *vfail = 1;
                                 ok = false;
@@ -552,7 +594,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float racc[DRAIN ? NSL : 1][SLW];   // running sums of the chunks (DRAIN only)
         bool ok = true;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-            const int z = t / tiles_mn, rem = t % tiles_mn;
+            int lt;
+            const KParams& p = P[locate(t, lt)];
+            const int ntm = (p.M + TM - 1) / TM, ntn = (p.N + p.bn - 1) / p.bn, tiles_mn = ntm * ntn;
+            const int z = lt / tiles_mn, rem = lt % tiles_mn;
             const int m0 = (p.nfast ? rem / ntn : rem % ntm) * TM, n0 = (p.nfast ? rem % ntn : rem / ntm) * p.bn;
             const int bz = z / p.ksplit, ks = z % p.ksplit;
             const int nk = min(p.per_split, p.nkb_total - ks * p.per_split);
@@ -581,7 +626,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             for (int c = 0; c < nch; ++c, ++li) {
                 const int buf = li & 1;
-                if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1), p.wait_ns)) {
+                if (!mbar_wait(tfull0 + 8u * buf, (uint32_t)((li >> 1) & 1), wait_ns)) {
                     if (lane == 0) atomicOr(p.err, 4u);
                     *vfail = 1;
                     ok = false;
@@ -656,11 +701,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         // every MMA of this block has completed before TMEM is released
-        if (!mbar_wait(drain_bar, 0, p.wait_ns)) atomicOr(p.err, 32u);
+        if (!mbar_wait(drain_bar, 0, wait_ns))
+            for (int q = 0; q < nprob; ++q) atomicOr(P[q].err, 32u);
         if (*vfail) {
             // loads issued but never consumed must land before the block exits
             for (int it = s_consumed; it < s_issued; ++it)
-                if (!mbar_wait(full0 + 8u * (it % S), (uint32_t)((it / S) & 1), p.wait_ns)) break;
+                if (!mbar_wait(full0 + 8u * (it % S), (uint32_t)((it / S) & 1), wait_ns)) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -670,6 +716,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
 }
+
+template <int PREC, bool DRAIN>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__ TcArgs a) {
+    tc_body<PREC, DRAIN>(&a.p, a.m, nullptr, 1, a.p.bn, a.p.stages, a.p.acc_cols, a.p.wait_ns);
+}
+
+template <int PREC, bool DRAIN>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm_group(const __grid_constant__ TcGroupArgs g) {
+    tc_body<PREC, DRAIN>(g.p, &g.m[0][0], g.tile0, g.n, g.bn_max, g.stages, g.acc_cols, g.wait_ns);
+}
+
+// the single-contraction kernels and their grouped counterparts
+const void* const k_single[6] = {(const void*)k_tc_gemm<PPL_PREC_BF16X3, false>, (const void*)k_tc_gemm<PPL_PREC_BF16X3, true>,
+                                 (const void*)k_tc_gemm<PPL_PREC_TF32, false>,   (const void*)k_tc_gemm<PPL_PREC_TF32, true>,
+                                 (const void*)k_tc_gemm<PPL_PREC_TF32X3, false>, (const void*)k_tc_gemm<PPL_PREC_TF32X3, true>};
+const void* const k_grouped[6] = {
+    (const void*)k_tc_gemm_group<PPL_PREC_BF16X3, false>, (const void*)k_tc_gemm_group<PPL_PREC_BF16X3, true>,
+    (const void*)k_tc_gemm_group<PPL_PREC_TF32, false>,   (const void*)k_tc_gemm_group<PPL_PREC_TF32, true>,
+    (const void*)k_tc_gemm_group<PPL_PREC_TF32X3, false>, (const void*)k_tc_gemm_group<PPL_PREC_TF32X3, true>};
 
 // Sum split-K partials part[ks][n][m] (fp32) in FP64 into out[m * ldo + n].
 __global__ void k_reduce_partials(const float* part, int ksplit, int M, int N, double* out, long long ldo) {
@@ -786,33 +851,7 @@ __global__ void k_split_panels(SplitSrc s, int rows, int prow, int cols, int kdi
 // X_b[a][k] in [b][k / KE][a][k % KE] (A rows per panel, k < B) ->
 // [b][a / KE][k][a % KE] (B rows per panel), through a KE x KE tile in shared
 // memory: both sides read and write whole contiguous KE-element rows.
-template <typename T, int PLANES, int KE>
-__global__ void k_transpose_panels(const T* src, T* dst, long long plane_s, long long plane_d, int A, int B,
-                                   long long bstride_s, long long bstride_d) {
-    __shared__ T tile[PLANES][KE][KE + 1];
-    const int b = blockIdx.z;
-    const int a0 = blockIdx.y * KE, k0 = blockIdx.x * KE;    // this block: a in [a0, a0+KE), k in [k0, k0+KE)
-    if (a0 >= A || k0 >= B) return;
-    const long long os = (long long)b * bstride_s, od = (long long)b * bstride_d;
-    const long long pan_s = (long long)A * KE, pan_d = (long long)B * KE;
-    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
-        const int ai = e / KE, ki = e % KE;          // reads: k fastest
-        const int a = a0 + ai, k = k0 + ki;
-        for (int pl = 0; pl < PLANES; ++pl)
-            tile[pl][ai][ki] = (a < A && k < B) ? src[pl * plane_s + os + (long long)(k / KE) * pan_s + (long long)a * KE + k % KE]
-                                                : T(0);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
-        const int ki = e / KE, ai = e % KE;          // writes: a fastest
-        const int a = a0 + ai, k = k0 + ki;
-        if (a < A && k < B)
-            for (int pl = 0; pl < PLANES; ++pl)
-                dst[pl * plane_d + od + (long long)(a / KE) * pan_d + (long long)k * KE + a % KE] = tile[pl][ai][ki];
-    }
-}
-
-// The same for 4-byte elements (KE = 32) with 16-byte accesses: thread t reads
+// 4-byte elements (KE = 32) with 16-byte accesses: thread t reads
 // row a0 + t / 8, elements 4 (t % 8) .. + 3 of a tile's 128-byte source row and
 // writes row k0 + t / 8, elements 4 (t % 8) .. + 3 of a destination row; the
 // padded shared tile makes both sides conflict-free.  vec = 0 (offsets that are
@@ -855,6 +894,73 @@ __global__ void __launch_bounds__(256) k_transpose_panels4(const float* src, flo
         for (int pl = 0; pl < PLANES; ++pl)
             tile[pl][ai][ki] = (a < A && k < B) ? src[pl * plane_s + os + (long long)blockIdx.x * pan_s + (long long)a * KE + ki]
                                                 : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int ki = e / KE, ai = e % KE;
+        const int a = a0 + ai, k = k0 + ki;
+        if (a < A && k < B)
+            for (int pl = 0; pl < PLANES; ++pl)
+                dst[pl * plane_d + od + (long long)blockIdx.y * pan_d + (long long)k * KE + ai] = tile[pl][ai][ki];
+    }
+}
+
+// The same for 2-byte elements (bf16, KE = 64): 64 x 64 tiles, thread t moves
+// elements 8 (t % 8) .. + 7 of rows t / 8 and 32 + t / 8 as 16-byte accesses;
+// the shared tile's rows are 33 words, so both sides are nearly conflict-free.
+template <int PLANES>
+__global__ void __launch_bounds__(256) k_transpose_panels_h(const unsigned short* src, unsigned short* dst,
+                                                            long long plane_s, long long plane_d, int A, int B,
+                                                            long long bstride_s, long long bstride_d, int vec) {
+    constexpr int KE = 64;
+    __shared__ unsigned short tile[PLANES][KE][KE + 2];
+    const int b = blockIdx.z;
+    const int a0 = blockIdx.y * KE, k0 = blockIdx.x * KE;
+    if (a0 >= A || k0 >= B) return;
+    const long long os = (long long)b * bstride_s, od = (long long)b * bstride_d;
+    const long long pan_s = (long long)A * KE, pan_d = (long long)B * KE;
+    if (vec && a0 + KE <= A && k0 + KE <= B) {
+        const int r = threadIdx.x >> 3, q = (threadIdx.x & 7) * 8;
+        uint4 v[PLANES][2];
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                v[pl][h] = *(const uint4*)(src + pl * plane_s + os + (long long)blockIdx.x * pan_s +
+                                           (long long)(a0 + r + 32 * h) * KE + q);
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t w[4] = {v[pl][h].x, v[pl][h].y, v[pl][h].z, v[pl][h].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    tile[pl][r + 32 * h][q + 2 * j] = (unsigned short)(w[j] & 0xffffu);
+                    tile[pl][r + 32 * h][q + 2 * j + 1] = (unsigned short)(w[j] >> 16);
+                }
+            }
+        __syncthreads();
+#pragma unroll
+        for (int pl = 0; pl < PLANES; ++pl)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kr = r + 32 * h;   // destination row k0 + kr, elements a0 + q .. + 7
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    w[j] = (uint32_t)tile[pl][q + 2 * j][kr] | ((uint32_t)tile[pl][q + 2 * j + 1][kr] << 16);
+                *(uint4*)(dst + pl * plane_d + od + (long long)blockIdx.y * pan_d + (long long)(k0 + kr) * KE + q) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        return;
+    }
+    for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
+        const int ai = e / KE, ki = e % KE;
+        const int a = a0 + ai, k = k0 + ki;
+        for (int pl = 0; pl < PLANES; ++pl)
+            tile[pl][ai][ki] = (a < A && k < B)
+                                   ? src[pl * plane_s + os + (long long)blockIdx.x * pan_s + (long long)a * KE + ki]
+                                   : (unsigned short)0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < KE * KE; e += blockDim.x) {
@@ -922,9 +1028,11 @@ int tc_init_driver() {
     g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     static bool attr_done = false;
     if (!attr_done) {
-        const void* fns[6] = {(const void*)k_tc_gemm<PPL_PREC_BF16X3, false>, (const void*)k_tc_gemm<PPL_PREC_BF16X3, true>,
-                              (const void*)k_tc_gemm<PPL_PREC_TF32, false>,   (const void*)k_tc_gemm<PPL_PREC_TF32, true>,
-                              (const void*)k_tc_gemm<PPL_PREC_TF32X3, false>, (const void*)k_tc_gemm<PPL_PREC_TF32X3, true>};
+        const void* fns[12];
+        for (int i = 0; i < 6; ++i) {
+            fns[i] = k_single[i];
+            fns[6 + i] = k_grouped[i];
+        }
         for (const void* f : fns) {
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_ATTR) != cudaSuccess) {
                 cudaGetLastError();
@@ -947,13 +1055,13 @@ int tc_init_driver() {
 namespace {
 
 template <int PREC>
-void launch_tc(bool drain, int grid, size_t smem, cudaStream_t s, const CUtensorMap& a, const CUtensorMap& al,
-               const CUtensorMap& b, const CUtensorMap& bl, const KParams& p) {
+void launch_tc(bool drain, int grid, size_t smem, cudaStream_t s, const TcArgs& a) {
     if (drain)
-        k_tc_gemm<PREC, true><<<grid, NTHREADS, smem, s>>>(a, al, b, bl, p);
+        k_tc_gemm<PREC, true><<<grid, NTHREADS, smem, s>>>(a);
     else
-        k_tc_gemm<PREC, false><<<grid, NTHREADS, smem, s>>>(a, al, b, bl, p);
+        k_tc_gemm<PREC, false><<<grid, NTHREADS, smem, s>>>(a);
 }
+
 
 }  // namespace
 
@@ -1006,7 +1114,8 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     p.err = err_flag;
     p.wait_ns = g.wait_ns > 0 ? g.wait_ns : WAIT_NS;
 
-    CUtensorMap mAh, mAl, mBh, mBl;
+    TcArgs a;
+    CUtensorMap &mAh = a.m[0], &mAl = a.m[1], &mBh = a.m[2], &mBl = a.m[3];
     const size_t es = half ? 2 : 4;
     if (!make_map(&mAh, g.prec, g.A.ptr, g.A, TM) || !make_map(&mBh, g.prec, g.B.ptr, g.B, p.bn)) return -3;
     if (split) {
@@ -1017,6 +1126,7 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
         mAl = mAh;
         mBl = mBh;
     }
+    a.p = p;
     const size_t smem = (size_t)stage_bytes * p.stages + 1024 + 16 * p.stages + 64;
     if (smem > (size_t)SMEM_ATTR) return -6;
     const long long tiles = (long long)((g.M + TM - 1) / TM) * ((g.N + p.bn - 1) / p.bn) * g.batch * p.ksplit;
@@ -1024,11 +1134,11 @@ int tc_gemm(const TcGemm& g, unsigned int* err_flag, cudaStream_t s) {
     int grid = (int)(tiles < sms ? tiles : sms);
     if (g.grid_cap > 0 && grid > g.grid_cap) grid = g.grid_cap;
     if (g.prec == PPL_PREC_BF16X3)
-        launch_tc<PPL_PREC_BF16X3>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
+        launch_tc<PPL_PREC_BF16X3>(drain, grid, smem, s, a);
     else if (g.prec == PPL_PREC_TF32X3)
-        launch_tc<PPL_PREC_TF32X3>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
+        launch_tc<PPL_PREC_TF32X3>(drain, grid, smem, s, a);
     else
-        launch_tc<PPL_PREC_TF32>(drain, grid, smem, s, mAh, mAl, mBh, mBl, p);
+        launch_tc<PPL_PREC_TF32>(drain, grid, smem, s, a);
     const cudaError_t le = cudaGetLastError();
     return le == cudaSuccess ? 0 : -(1000 + (int)le);
 }
@@ -1091,8 +1201,11 @@ void transpose_panels(int prec, const void* src, void* dst, long long plane_s, l
                       long long bstride_s, long long bstride_d, int batch, cudaStream_t s) {
     if (A <= 0 || B <= 0 || batch <= 0) return;
     if (prec == PPL_PREC_BF16X3) {
-        k_transpose_panels<unsigned short, 2, 64><<<dim3((B + 63) / 64, (A + 63) / 64, batch), 256, 0, s>>>(
-            (const unsigned short*)src, (unsigned short*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d);
+        auto m8 = [](long long x) { return x % 8 == 0; };
+        const int vec = m8(plane_s) && m8(plane_d) && m8(bstride_s) && m8(bstride_d) &&
+                        (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0;
+        k_transpose_panels_h<2><<<dim3((B + 63) / 64, (A + 63) / 64, batch), 256, 0, s>>>(
+            (const unsigned short*)src, (unsigned short*)dst, plane_s, plane_d, A, B, bstride_s, bstride_d, vec);
     } else {
         auto m4 = [](long long x) { return x % 4 == 0; };
         const int vec = m4(plane_s) && m4(plane_d) && m4(bstride_s) && m4(bstride_d) &&
@@ -1110,3 +1223,77 @@ void transpose_panels(int prec, const void* src, void* dst, long long plane_s, l
 void zero_bytes(void* p, size_t n, cudaStream_t s) {
     if (n) cudaMemsetAsync(p, 0, n, s);
 }
+
+// ---- several captured contractions as one persistent launch ------------------
+
+namespace {
+struct GroupNode {
+    TcGroupArgs a;
+    void* params[1];
+};
+}  // namespace
+
+const void* tc_group_kernel(const void* f) {
+    for (int i = 0; i < 6; ++i)
+        if (k_single[i] == f) return k_grouped[i];
+    return nullptr;
+}
+
+int tc_group_capacity() { return TC_GROUP_MAX; }
+
+int tc_group_node_params(const void* f, const void* const* args, int n, cudaKernelNodeParams* out, void** storage) {
+    *storage = nullptr;
+    int ki = -1;
+    for (int i = 0; i < 6; ++i)
+        if (k_single[i] == f) ki = i;
+    if (ki < 0 || n < 1 || n > TC_GROUP_MAX || !args || !out) return -1;
+    if (tc_init_driver() != 0) return -1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) return -7;
+    GroupNode* g = new (std::nothrow) GroupNode();
+    if (!g) return -2;
+    TcGroupArgs& a = g->a;
+    a.n = n;
+    a.bn_max = 0;
+    a.acc_cols = 0;
+    a.wait_ns = 0;
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) {
+        const TcArgs* x = (const TcArgs*)args[i];
+        for (int j = 0; j < 4; ++j) a.m[i][j] = x->m[j];
+        a.p[i] = x->p;
+        if (x->p.bn > a.bn_max) a.bn_max = x->p.bn;
+        if (x->p.acc_cols > a.acc_cols) a.acc_cols = x->p.acc_cols;
+        if (x->p.wait_ns > a.wait_ns) a.wait_ns = x->p.wait_ns;
+        a.tile0[i] = (int)tot;
+        tot += tc_tiles(x->p);
+    }
+    if (tot > (1ll << 30)) {
+        delete g;
+        return -4;
+    }
+    a.tile0[n] = (int)tot;
+    const int planes = (ki / 2 == 1) ? 1 : 2;   // TF32 one plane; BF16X3 and TF32X3 hi and lo
+    const int stage_bytes = planes * (TM + a.bn_max) * KROW_BYTES;
+    a.stages = SMEM_BUDGET / stage_bytes;
+    if (a.stages > 8) a.stages = 8;
+    const size_t smem = (size_t)stage_bytes * a.stages + 1024 + 16 * a.stages + 64;
+    if (a.stages < 2 || smem > (size_t)SMEM_ATTR) {
+        delete g;
+        return -6;
+    }
+    g->params[0] = &g->a;
+    *out = cudaKernelNodeParams{};
+    out->func = const_cast<void*>(k_grouped[ki]);
+    out->gridDim = dim3((unsigned)(tot < sms ? tot : sms));
+    out->blockDim = dim3(NTHREADS);
+    out->sharedMemBytes = (unsigned)smem;
+    out->kernelParams = g->params;
+    out->extra = nullptr;
+    *storage = g;
+    return 0;
+}
+
+void tc_group_release(void* storage) { delete (GroupNode*)storage; }

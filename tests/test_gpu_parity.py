@@ -338,6 +338,12 @@ def test_batch_of_uneven_instances_equals_individual_sweeps():
         for k in fp:
             check_columns(fp[k].reshape(-1, fp[k].shape[-1]), fq[k].reshape(-1, fq[k].shape[-1]), 1e-12,
                           f"batch vs solo {k}")
+    # the batch graph solves each mode of all instances in one launch (plus its
+    # barrier reset) and runs contractions of equal depth in grouped launches: at
+    # least the first contraction of every instance (T of mode a) shares one
+    n = len(probs)
+    solo_kernels = sum(int(q.stats()["kernels_per_sweep"]) for q in solo)
+    assert batch.kernels_per_sweep() <= solo_kernels - 4 * n + 8 - (n - 1), (batch.kernels_per_sweep(), solo_kernels)
     batch.close()
     for p in probs + solo:
         p.close()
