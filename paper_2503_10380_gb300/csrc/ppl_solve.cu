@@ -23,6 +23,8 @@
 // all blocks observe, records the error and returns.
 #include "ppl_internal.h"
 
+#include <algorithm>
+
 #include <cmath>
 
 namespace {
@@ -755,20 +757,28 @@ __device__ __forceinline__ void solve_body(const SolveP& p, const int bid, const
 
 __global__ void __launch_bounds__(NT, 1) k_solve(const __grid_constant__ SolveP p) { solve_body(p, blockIdx.x, gridDim.x); }
 
-// Several instances' mode updates in one cooperative launch: instance k runs on
-// blocks blk0[k] .. blk0[k+1]-1 with its own barrier words, so the instances
-// proceed independently and only share the SMs.
+// Several instances' mode updates in one cooperative launch.  The blocks form
+// lanes: lane l is blocks lane_blk0[l] .. lane_blk0[l+1]-1 and solves the
+// instances order[lane_inst0[l]] .. order[lane_inst0[l+1]-1] one after the
+// other, each with its own barrier words, so the lanes proceed independently
+// and only share the SMs.
 constexpr int MAX_BATCH = 64;
 struct SolveBatch {
-    int n;
-    int blk0[MAX_BATCH + 1];
+    int n, nl;
+    int lane_blk0[MAX_BATCH + 1];
+    int lane_inst0[MAX_BATCH + 1];
+    int order[MAX_BATCH];
     SolveP p[MAX_BATCH];
 };
 
 __global__ void __launch_bounds__(NT, 3) k_solve_batch(const __grid_constant__ SolveBatch b) {
-    int k = 0;
-    while (k + 1 < b.n && b.blk0[k + 1] <= (int)blockIdx.x) ++k;
-    solve_body(b.p[k], (int)blockIdx.x - b.blk0[k], b.blk0[k + 1] - b.blk0[k]);
+    int l = 0;
+    while (l + 1 < b.nl && b.lane_blk0[l + 1] <= (int)blockIdx.x) ++l;
+    const int bid = (int)blockIdx.x - b.lane_blk0[l], G = b.lane_blk0[l + 1] - b.lane_blk0[l];
+    for (int i = b.lane_inst0[l]; i < b.lane_inst0[l + 1]; ++i) {
+        solve_body(b.p[b.order[i]], bid, G);
+        __syncthreads();   // the block's shared memory is reused by the next instance
+    }
 }
 
 // the barrier words and the diagonal maximum of every instance start at zero
@@ -867,44 +877,62 @@ int solve_modes_batched(const SolveArgs* a, int n, cudaStream_t s) {
         if (2 * nb > cap) return -3;
         SolveBatch b;
         b.n = nb;
-        int want[MAX_BATCH], alloc[MAX_BATCH];
-        long long total = 0;
-        double wsum = 0.0, work[MAX_BATCH];
+        int want[MAX_BATCH];
+        double work[MAX_BATCH], steps[MAX_BATCH];
         for (int k = 0; k < nb; ++k) {
             const SolveArgs& x = a[k0 + k];
             want[k] = solve_want(x.dim, x.R, sms);
-            total += want[k];
             work[k] = (double)x.R * x.R * x.R / 3.0 + 4.0 * x.dim * (double)x.R * x.R;
-            wsum += work[k];
+            steps[k] = (double)((x.R + NB - 1) / NB);
+            b.p[k] = to_params(x);
         }
-        if (total <= cap) {
-            for (int k = 0; k < nb; ++k) alloc[k] = want[k];
-        } else {
-            // share the co-resident blocks out by FP64 work, at least 2 per instance
-            const int spare = cap - 2 * nb;
-            long long used = 0;
+        // Lanes: L lanes of cap / L blocks; each instance goes to one lane, longest
+        // first to the least loaded.  Modelled time of an instance on G blocks: its
+        // FP64 work at G blocks' share of the FP64 rate (2 FMA per clock per SM at
+        // about 2 GHz, shared by the blocks of an SM) plus a latency per 32-wide
+        // block step; L is the one with the shortest modelled makespan.
+        const double rate_blk = 8.0e9 / g_batch_per_sm, step_s = 20e-6;
+        auto est = [&](int k, int G) { return work[k] / ((double)(G < want[k] ? G : want[k]) * rate_blk) + steps[k] * step_s; };
+        int best_L = 0, best_lane[MAX_BATCH] = {};
+        double best_span = 0.0;
+        for (int L = 1; L <= nb; ++L) {
+            const int W = cap / L;
+            if (W < 2) break;
+            int idx[MAX_BATCH], lane[MAX_BATCH];
+            double t[MAX_BATCH], load[MAX_BATCH];
             for (int k = 0; k < nb; ++k) {
-                int g = 2 + (int)((double)spare * work[k] / wsum);
-                if (g > want[k]) g = want[k];
-                alloc[k] = g;
-                used += g;
+                idx[k] = k;
+                t[k] = est(k, W);
             }
-            while (used > cap) {   // rounding cannot overshoot, but keep the launch valid regardless
-                int big = 0;
-                for (int k = 1; k < nb; ++k)
-                    if (alloc[k] > alloc[big]) big = k;
-                if (alloc[big] <= 2) return -3;
-                --alloc[big];
-                --used;
+            std::sort(idx, idx + nb, [&](int x, int y) { return t[x] > t[y]; });
+            for (int l = 0; l < L; ++l) load[l] = 0.0;
+            for (int q = 0; q < nb; ++q) {
+                int lmin = 0;
+                for (int l = 1; l < L; ++l)
+                    if (load[l] < load[lmin]) lmin = l;
+                lane[idx[q]] = lmin;
+                load[lmin] += t[idx[q]];
+            }
+            double span = 0.0;
+            for (int l = 0; l < L; ++l) span = load[l] > span ? load[l] : span;
+            if (best_L == 0 || span < best_span) {
+                best_L = L;
+                best_span = span;
+                for (int k = 0; k < nb; ++k) best_lane[k] = lane[k];
             }
         }
-        int blk = 0;
-        for (int k = 0; k < nb; ++k) {
-            b.blk0[k] = blk;
-            b.p[k] = to_params(a[k0 + k]);
-            blk += alloc[k];
+        if (best_L == 0) return -3;
+        b.nl = best_L;
+        int blk = 0, q = 0;
+        for (int l = 0; l < best_L; ++l) {
+            b.lane_blk0[l] = blk;
+            blk += cap / best_L + (l < cap % best_L ? 1 : 0);
+            b.lane_inst0[l] = q;
+            for (int k = 0; k < nb; ++k)
+                if (best_lane[k] == l) b.order[q++] = k;
         }
-        b.blk0[nb] = blk;
+        b.lane_blk0[best_L] = blk;
+        b.lane_inst0[best_L] = q;
         k_solve_batch_prep<<<1, MAX_BATCH, 0, s>>>(b);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blk);
