@@ -227,13 +227,18 @@ int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out);
 typedef struct ppl_cpd_batch ppl_cpd_batch;   /* opaque, host memory owned by the library */
 
 /* Group n handles (each from ppl_cpd_init with its own workspace, sizes may
- * differ) so that one sweep of every instance runs from a single CUDA graph:
- * instance k is issued on internal stream k % nstreams, all forked from and
- * joined back to `stream`.  While in a batch, each handle's cooperative
- * solve and each of its tensor-core contractions use at most about
- * 4/nstreams of the SMs, so that the work of several instances can overlap
- * (reset by ppl_cpd_batch_destroy).  The
- * handles stay owned by the caller and must outlive the batch. */
+ * differ; one precision and accumulation setting for all) so that one sweep of
+ * every instance runs from a single CUDA graph, forked from and joined back to
+ * `stream`: every instance is captured on its own internal stream, then the
+ * instances' tensor-core contractions of equal depth in their chains run as
+ * grouped persistent launches (up to 40 contractions each), and each mode's
+ * solves of all instances (at most 64 per launch) as one cooperative launch
+ * whose blocks form lanes that solve their instances in turn (the Role of the
+ * Initial Guess section motivates many CPDs per CC iteration; the grouping has
+ * no counterpart in the paper).  nstreams >= 1 sets the share of the SMs, about
+ * 4/nstreams, that a contraction left out of a group may use (reset by
+ * ppl_cpd_batch_destroy).  The handles stay owned by the caller and must
+ * outlive the batch. */
 int ppl_cpd_batch_create(ppl_cpd_batch** b, int n, ppl_cpd* const* handles, int nstreams, void* stream);
 
 /* nsweeps sweeps of every instance; fits (HOST, may be NULL) receives
