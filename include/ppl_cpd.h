@@ -226,8 +226,8 @@ int ppl_cpd_autotune(ppl_cpd* h, int* r_chunk_out);
 
 typedef struct ppl_cpd_batch ppl_cpd_batch;   /* opaque, host memory owned by the library */
 
-/* Group n handles (each from ppl_cpd_init with its own workspace, sizes may
- * differ; one precision and accumulation setting for all) so that one sweep of
+/* Group n handles (each from ppl_cpd_init with its own workspace; sizes and
+ * options may differ, and only contractions of the same kernel are grouped) so that one sweep of
  * every instance runs from a single CUDA graph, forked from and joined back to
  * `stream`: every instance is captured on its own internal stream, then the
  * instances' tensor-core contractions of equal depth in their chains run as
