@@ -53,6 +53,11 @@ extern "C" {
                               accumulate restarted every acc_chunk K blocks and summed
                               with round-to-nearest                                        */
 
+/* initial guess of ppl_cpd_init (the Role of the Initial Guess section: a random start) */
+#define PPL_INIT_USER    0  /* the factors buffer holds the caller's guess                     */
+#define PPL_INIT_NORMAL  1  /* U_a, U_b, U_i, U_j filled on the device with N(0, 1) numbers     */
+#define PPL_INIT_UNIFORM 2  /* the same with uniform numbers in [0, 1)                          */
+
 #define PPL_MODE_A 0  /* alpha, first virtual index  */
 #define PPL_MODE_B 1  /* beta, second virtual index  */
 #define PPL_MODE_I 2  /* gamma, first occupied index  */
@@ -83,9 +88,21 @@ typedef struct {
                         after this many microseconds; 0 = 1 s for the solve, 0.5 s for
                         the pipeline.  On expiry the kernel records the error, drains
                         what it issued and returns; the call reports PPL_ETIMEOUT.     */
-    int acc_steps_p; /* as acc_steps, for the contractions of the S-build (W_b, S, P),
-                        whose result M_j sets lam and so the energy; 0 = as acc_steps */
-    int reserved[6];
+    int acc_steps_p; /* as acc_steps, for the contractions of the S-build (W_b, S, P, and
+                        W_a, which it then forms itself instead of taking the mode-b
+                        chain's), whose result M_j sets lam and so the energy; 0 = as
+                        acc_steps                                                       */
+    int init;        /* PPL_INIT_*: with NORMAL or UNIFORM, ppl_cpd_init overwrites the
+                        factors buffer: element e of U_a, U_b, U_i, U_j (in that order,
+                        each [dim][R] row-major, e counted over all four) is, from the
+                        counter-based splitmix64 generator (Steele, Lea & Flood 2014) with
+                        key = mix(init_seed ^ 4 * 0xD1B54A32D192ED03) and uniforms
+                        u_k = (mix(key + (k + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53,
+                        NORMAL: sqrt(-2 log1p(-u_2e)) cos(2 pi u_2e+1) (Box-Muller),
+                        UNIFORM: u_e.  The same numbers as the seeded synthetic inputs'
+                        initial factors (up to the last bits of log1p and cos).         */
+    int init_seed;   /* seed of the NORMAL / UNIFORM guess (taken as unsigned)          */
+    int reserved[4];
 } ppl_cpd_opts;
 
 typedef struct {

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "PPL_OK", 1: "PPL_EINVAL", 2: "PPL_ENOMEM", 3: "PPL_ECUDA", 4
 class ppl_cpd_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("r_chunk", c_int), ("use_graph", c_int), ("want_eta", c_int),
                 ("profile", c_int), ("dressed", c_int), ("acc_chunk", c_int), ("acc_steps", c_int),
-                ("wait_limit_us", c_int), ("acc_steps_p", c_int), ("reserved", c_int * 6)]
+                ("wait_limit_us", c_int), ("acc_steps_p", c_int), ("init", c_int), ("init_seed", c_int),
+                ("reserved", c_int * 4)]
 
 
 class ppl_cpd_stats(ctypes.Structure):
@@ -110,8 +111,12 @@ def _check(rc: int, h=None):
         raise PplError(rc, msg.decode() if msg else "")
 
 
+INIT = {"user": 0, "normal": 1, "uniform": 2}
+
+
 def make_opts(precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False, profile=False,
-              dressed=False, acc_chunk=0, acc_steps=0, wait_limit_us=0, acc_steps_p=0) -> ppl_cpd_opts:
+              dressed=False, acc_chunk=0, acc_steps=0, wait_limit_us=0, acc_steps_p=0,
+              init="user", init_seed=0) -> ppl_cpd_opts:
     o = ppl_cpd_opts()
     lib().ppl_cpd_default_opts(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -124,6 +129,8 @@ def make_opts(precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False, pro
     o.acc_steps = int(acc_steps)
     o.wait_limit_us = int(wait_limit_us)
     o.acc_steps_p = int(acc_steps_p)
+    o.init = INIT[init] if isinstance(init, str) else int(init)
+    o.init_seed = ctypes.c_int(int(init_seed) & 0xFFFFFFFF).value
     return o
 
 
@@ -317,29 +324,34 @@ class CpAls:
 
     B [X][o+v][o+v] and tau [o][o][v][v] are FP64 device tensors (kept alive
     here); `factors` is a dict of initial guesses "a","b" [v][R] and "i","j"
-    [o][R] (numpy or torch).  torch allocates the factor buffer and the
-    workspace; the library does the rest.
+    [o][R] (numpy or torch), or, with init="normal" or "uniform", the rank R
+    as an int (the library then draws the guess on the device from init_seed).
+    torch allocates the factor buffer and the workspace; the library does the
+    rest.
     """
 
     def __init__(self, B, tau, factors, precision="tf32x3", r_chunk=0, use_graph=True, want_eta=False,
                  profile=False, dressed=False, stream=None, acc_chunk=0, acc_steps=0, wait_limit_us=0,
-                 acc_steps_p=0):
+                 acc_steps_p=0, init="user", init_seed=0):
         import torch
         self.torch = torch
         X, n, _ = B.shape
         o = tau.shape[0]
         v = tau.shape[2]
-        R = factors["a"].shape[1]
+        R = int(factors) if isinstance(factors, int) else factors["a"].shape[1]
         assert n == o + v and B.dtype == torch.float64 and tau.dtype == torch.float64 and B.is_cuda
         self.o, self.v, self.X, self.R = o, v, X, R
         self.B = B.contiguous()
         self.tau = tau.contiguous()
         dev = B.device
-        parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
-        parts.append(torch.ones(R, dtype=torch.float64))
-        self.fac = torch.cat(parts).to(dev)
+        if isinstance(factors, int):
+            self.fac = torch.zeros((2 * v + 2 * o + 1) * R, dtype=torch.float64, device=dev)
+        else:
+            parts = [torch.as_tensor(factors[m], dtype=torch.float64).reshape(-1) for m in ("a", "b", "i", "j")]
+            parts.append(torch.ones(R, dtype=torch.float64))
+            self.fac = torch.cat(parts).to(dev)
         self.opts = make_opts(precision, r_chunk, use_graph, want_eta, profile, dressed, acc_chunk, acc_steps,
-                              wait_limit_us, acc_steps_p)
+                              wait_limit_us, acc_steps_p, init, init_seed)
         self.ws_bytes = ppl_cpd_workspace_size(o, v, X, R, self.opts)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)

@@ -1022,6 +1022,8 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     ppl_cpd_default_opts(&op);
     if (opts) op = *opts;
     if (op.precision < 0 || op.precision > 3) return fail(nullptr, PPL_EINVAL, "unknown precision %d", op.precision);
+    if (op.init < PPL_INIT_USER || op.init > PPL_INIT_UNIFORM)
+        return fail(nullptr, PPL_EINVAL, "unknown initial guess %d", op.init);
     if (!B || !tau || !factors || !workspace) return fail(nullptr, PPL_EINVAL, "NULL device pointer");
     if (((uintptr_t)workspace) % 256) return fail(nullptr, PPL_EINVAL, "workspace not 256-byte aligned");
     Layout L;
@@ -1075,6 +1077,10 @@ int ppl_cpd_init(ppl_cpd** hp, int o, int v, int X, int R, const double* B, cons
     if (!e) {
         cudaMemsetAsync(h->ws + L.scal, 0, NSCAL * sizeof(double), h->st);
         cudaMemsetAsync(h->ws + L.flags, 0, 64, h->st);
+        // the stream of the seeded synthetic inputs' initial factors (id 4)
+        if (op.init != PPL_INIT_USER)
+            fill_random(h->fac, (long long)(2 * v + 2 * o) * R, op.init == PPL_INIT_NORMAL, (unsigned int)op.init_seed, 4,
+                        h->st);
         fill_f64(h->lam, (size_t)R, 1.0, h->st);
         cudaMemcpyAsync(h->ws + L.guess0, h->fac, h->fac_bytes(), cudaMemcpyDeviceToDevice, h->st);
         for (int m = 0; m < 4; ++m) gram(h, m);

@@ -482,3 +482,44 @@ extern "C" int ppl_probe_fp64_peak(double* tflops, void* stream) {
     *tflops = flops / (best * 1e-3) / 1e12;
     return PPL_OK;
 }
+
+// ---- seeded initial guess -----------------------------------------------------
+
+namespace {
+
+// splitmix64 finaliser (Steele, Lea & Flood, "Fast splittable pseudorandom
+// number generators", OOPSLA 2014)
+__host__ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// uniform number i (0-based) of the counter stream with this key, in [0, 1)
+__device__ __forceinline__ double sm64_u01(unsigned long long key, unsigned long long i) {
+    const unsigned long long x = sm64_mix(key + (i + 1ull) * 0x9E3779B97F4A7C15ull);
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_fill_random(double* f, long long n, int normal, unsigned long long key) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        if (normal) {
+            // Box-Muller, cosine branch: normal e from uniforms 2e and 2e + 1
+            const double u1 = sm64_u01(key, 2ull * (unsigned long long)e);
+            const double u2 = sm64_u01(key, 2ull * (unsigned long long)e + 1ull);
+            f[e] = sqrt(-2.0 * log1p(-u1)) * cos(6.283185307179586 * u2);
+        } else {
+            f[e] = sm64_u01(key, (unsigned long long)e);
+        }
+    }
+}
+
+}  // namespace
+
+void fill_random(double* f, long long n, int normal, unsigned int seed, int stream_id, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned long long key = sm64_mix((unsigned long long)seed ^ ((unsigned long long)stream_id * 0xD1B54A32D192ED03ull));
+    long long g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_fill_random<<<(int)g, 256, 0, s>>>(f, n, normal, key);
+}

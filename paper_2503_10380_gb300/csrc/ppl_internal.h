@@ -84,6 +84,9 @@ void kr_pair(const double* U1, const double* U2, const double* lam, int d1, int 
 // X[a][b][i][j] <- 0.5 (X[a][b][i][j] + X[b][a][j][i]) in place
 void symmetrise_pairs(double* X, int v, int o, cudaStream_t s);
 void fill_f64(double* p, size_t n, double val, cudaStream_t s);
+// f[e], e < n: N(0,1) (normal = 1, Box-Muller) or U[0,1) numbers of the counter-
+// based splitmix64 stream (seed, stream_id); see ppl_cpd_opts.init
+void fill_random(double* f, long long n, int normal, unsigned int seed, int stream_id, cudaStream_t s);
 // out[Q][b][d] = B[Q][o+b][o+d]
 void extract_vv(const double* B, int o, int v, int X, double* out, cudaStream_t s);
 

@@ -97,6 +97,23 @@ def test_init_rejects_small_workspace_and_null(lib):
     assert lib.ppl_cpd_destroy(None) == binding.PPL_OK
 
 
+def test_init_guess_options(lib):
+    """The options struct keeps its size (16 ints: init and init_seed took two
+    of the reserved words) and an unknown guess kind is refused before any CUDA
+    call."""
+    assert ctypes.sizeof(binding.ppl_cpd_opts) == 16 * 4
+    assert binding.ppl_cpd_opts.init.offset == 10 * 4 and binding.ppl_cpd_opts.init_seed.offset == 11 * 4
+    opts = binding.make_opts("fp64", init="normal", init_seed=-1)
+    assert opts.init == 1 and opts.init_seed == -1          # the seed is taken as unsigned by the library
+    opts.init = 7
+    need = binding.ppl_cpd_workspace_size(5, 24, 72, 48, opts)
+    h = ctypes.c_void_p()
+    fake = 1 << 20
+    rc = lib.ppl_cpd_init(ctypes.byref(h), 5, 24, 72, 48, fake, fake, fake, fake, need, ctypes.byref(opts), None)
+    assert rc == binding.PPL_EINVAL
+    assert b"initial guess" in lib.ppl_last_error(None)
+
+
 def test_handle_calls_reject_null_handle(lib):
     x = ctypes.c_double()
     assert lib.ppl_cpd_fit(None, ctypes.byref(x)) == binding.PPL_EINVAL

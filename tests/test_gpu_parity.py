@@ -229,6 +229,39 @@ def test_sweeps_over_several_r_chunks(prec, ftol, acc_steps_p, dressed):
     cp.close()
 
 
+@pytest.mark.parametrize("kind", ["normal", "uniform"])
+def test_seeded_initial_guess_on_the_device(kind):
+    """init = NORMAL / UNIFORM draws U_a, U_b, U_i, U_j on the device from the
+    counter-based generator of the synthetic inputs (stream 4): NORMAL gives the
+    seeded initial factors of inputs.make_factors, UNIFORM the uniforms of the
+    same stream (bit-exact: integer mixing and one exact scaling; the normals
+    within the last bits of log1p and cos).  Sweeps then match oracle ALS from
+    that guess."""
+    o, v, X, R, seed = 5, 24, 72, 48, 11
+    inp = inputs.make_inputs(o, v, X, R, seed=0)
+    n = 2 * v * R + 2 * o * R
+    if kind == "normal":
+        ref = inputs.make_factors(seed, o, v, R)
+    else:
+        u = inputs.uniform(seed, inputs.STREAM_FACTORS, n)
+        ref, pos = {}, 0
+        for m, dim in (("a", v), ("b", v), ("i", o), ("j", o)):
+            ref[m] = u[pos:pos + dim * R].reshape(dim, R)
+            pos += dim * R
+    cp = binding.CpAls(_dev(inp.B), _dev(inp.tau), R, precision="fp64", init=kind, init_seed=seed)
+    f = _factors(cp)
+    for m in "abij":
+        if kind == "uniform":
+            assert np.array_equal(f[m], ref[m]), m
+        else:
+            assert np.max(np.abs(f[m] - ref[m])) <= 1e-13 * max(1.0, np.max(np.abs(ref[m]))), m
+    assert np.all(f["lam"] == 1.0)
+    U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, ref, 3)
+    cp.sweep(3)
+    _check_factors(_factors(cp), U_ref, lam_ref, 1e-8, f"fp64 sweeps from the {kind} device guess")
+    cp.close()
+
+
 def test_graph_replay_equals_direct_launches():
     inp = inputs.make_inputs(4, 20, 30, 40, seed=5)
     U_ref, lam_ref, _ = orc.cp_als(inp.Bvv, inp.tau, inp.factors, 3)
