@@ -546,6 +546,8 @@ def run_ours(args, world, rank, local):
     if not args.no_secondary:
         secondary["o=20 v=200 X=600 R=800"] = secondary_config(CFG1, args.precision, 30, 20, stream, dev, pk)
         secondary["o=40 v=400 X=1200 R=1600"] = secondary_config(CFG2, args.precision, 5, 10, stream, dev, pk)
+        # the batch of uneven instances in the precision its configuration names (BF16 split)
+        secondary["batch of 64"] = batch_secondary(dev, "bf16x3")
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) -----------
     cpu = None
@@ -709,6 +711,46 @@ def run_batch(args, world, rank, local):
         p.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batch_secondary(dev, precision, steps=3, warmup=3):
+    """The 64-instance batch (o in [4,24], v in [40,240], X = 3v, R in [2v,4v]) as a
+    secondary field of the main line: batch sweeps/s from CUDA events around
+    `steps` graph-replayed batch sweeps, launches per batch sweep and the whole-
+    sweep MTTKRP TFLOP/s.  Any failure is reported in the field, never raised."""
+    import torch
+    from paper_2503_10380_gb300 import binding, inputs
+    try:
+        shapes = inputs.batch_shapes(64, seed=SEED)
+        data = [inputs.make_inputs_torch(*sh, seed=SEED + k, device=dev) for k, sh in enumerate(shapes)]
+        flops = sum(alg_flops(*sh) for sh in shapes)
+        probs = []
+        for (B, tau, fac) in data:
+            cp = binding.CpAls(B, tau, fac, precision=precision)
+            cp.autotune()
+            probs.append(cp)
+        batch = binding.Batch(probs, nstreams=8)
+        batch.sweep(warmup, want_fits=False)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.sweep(steps, want_fits=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out = {"workload": "cp-als-ppl batch of 64 uneven instances (o 4-24, v 40-240, X = 3v, R 2v-4v), one graph",
+               "precision": precision, "batch_sweeps_per_s": 1000.0 / ms, "ms_per_batch_sweep": ms,
+               "sweep_tflops": flops / (ms / 1000.0) / 1e12, "launches_per_batch_sweep": int(batch.kernels_per_sweep())}
+        batch.close()
+        for p in probs:
+            p.close()
+        del data, probs
+        torch.cuda.empty_cache()
+        return out
+    except Exception as exc:   # a secondary field must not take the main line down
+        return {"error": f"{type(exc).__name__}: {exc}"}
 
 
 PREC_CFG, PREC_SWEEPS = (40, 400, 1200, 1600), 20
