@@ -160,7 +160,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 constexpr int RB = 256;      // threads per reduction block
-constexpr int RGRID = 304;   // 2 x 152 SMs
+// Blocks of the two-stage FP64 reductions (fit, eta, energy, exact contraction):
+// a fixed width, 2 x the 152 SMs of GB300, not a device query, so that the sums
+// are formed in the same order on every device (deterministic results) and the
+// workspace's partial-sum buffer (2 values per block) is sized by the host-side
+// planner, which runs without a device.
+constexpr int RGRID = 304;
 
 __global__ void __launch_bounds__(RB) k_fit_terms(const double* M, const double* U, const double* lam, int dim, int R,
                                                   const double* Ga, const double* Gb, const double* Gi,
